@@ -1,0 +1,231 @@
+/*
+ * icarus.h - C ABI of libicarus, a GB300 (sm_103a) implementation of the
+ * explicit finite-volume update of the Icarus heliospheric MHD model
+ * (arXiv 2211.12867): ideal MHD in the frame co-rotating with the Sun on a
+ * block-structured spherical (r, theta, phi) grid with radial stretching and
+ * solution-adaptive mesh refinement.
+ *
+ * Method passages (paper section / equation / table):
+ *   Sect. 2.1  ideal MHD in the co-rotating frame; TVDLF scheme, second order
+ *              in space and time, Woodward limiter, parabolic div B
+ *              cleaning; domain 0.1-2 AU, +-60 deg, 360 deg; two ghost
+ *              layers; inner boundary fixed in the rotating frame.
+ *   Eqs. 1-4   cone CME injected through the inner boundary.
+ *   Sect. 2.2, Eq. 5, Tables 1 and 3   radial grid stretching.
+ *   Sect. 3    block AMR: factor 2 per level in every direction, adjacent
+ *              blocks differ by at most one level, blocks coarsen again when
+ *              the criterion fails.
+ *
+ * Units.  Everything crossing this ABI is in normalised units: length 1 AU,
+ * speed 100 km/s, density m_p per cm^3, pressure rho0 v0^2, magnetic field
+ * sqrt(mu0 rho0 v0^2) (mu0 absorbed), time 1 AU / (100 km/s).  Angles are
+ * radians; theta is the colatitude.
+ *
+ * Variables.  Conserved U = (rho, m_r, m_th, m_ph, e, B_r, B_th, B_ph);
+ * primitive W = (rho, v_r, v_th, v_ph, p, B_r, B_th, B_ph); vector components
+ * in the local orthonormal basis.
+ *
+ * Host state layout.  State arrays exchanged with the host are FP64,
+ * [leaf][variable][i][j][k] over the interior cells of each leaf block, leaves
+ * of one member in Morton order (see icarus_get_tree), i = r index (slowest),
+ * k = phi index (fastest).
+ *
+ * Ownership.  The caller owns the device arena and the CUDA stream; the
+ * library allocates no device memory and keeps only small host-side
+ * bookkeeping behind the context.  Calls are asynchronous on the stream except
+ * those that return host data, which synchronise the stream.
+ *
+ * Errors.  Every call returns a status; nothing throws or exits.  Device
+ * kernels record non-physical states (NaN, density or pressure below the
+ * floors beyond the floor budget) in a sticky device word that is read at
+ * synchronising calls.  After ICARUS_ERR_NONPHYSICAL or ICARUS_ERR_TIMEOUT the
+ * context accepts only icarus_get_state, icarus_status_word and
+ * icarus_destroy.  One host thread per context; no internal locking.
+ */
+#ifndef ICARUS_H
+#define ICARUS_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct icarus_ctx icarus_ctx;
+
+typedef enum {
+  ICARUS_OK = 0,
+  ICARUS_ERR_ARG = 1,          /* invalid argument or descriptor */
+  ICARUS_ERR_ARENA = 2,        /* caller arena too small / misaligned */
+  ICARUS_ERR_CUDA = 3,         /* a CUDA runtime call failed */
+  ICARUS_ERR_NONPHYSICAL = 4,  /* NaN or floor budget exceeded on the device */
+  ICARUS_ERR_TIMEOUT = 5,      /* a bounded device wait gave up */
+  ICARUS_ERR_STATE = 6,        /* call out of order / context poisoned */
+  ICARUS_ERR_CAPACITY = 7      /* block pool too small for the refined tree */
+} icarus_status;
+
+enum { ICARUS_FP64 = 0, ICARUS_FP32_MIXED = 1 };
+enum { ICARUS_SPHERICAL = 0, ICARUS_CARTESIAN = 1 };
+enum { ICARUS_BC_PERIODIC = 0, ICARUS_BC_OUTFLOW = 1, ICARUS_BC_REFLECT = 2, ICARUS_BC_INNER = 3 };
+enum { ICARUS_FLAG_PLAIN = 0, ICARUS_FLAG_LEARNED = 1, ICARUS_FLAG_BOTH = 2 };
+
+/* Grid descriptor.
+ *   n_cells      base-level cells (r, theta, phi); must be multiples of block.
+ *   block        interior cells per block and direction, even, >= 4.
+ *   max_level    finest level (1 = no refinement); per member, see
+ *                icarus_set_member_max_level.  At most 8.
+ *   radial_stretch  1: geometric radial faces r_I = r_in (r_out/r_in)^(I/N)
+ *                (Sect. 2.2); 0: equidistant.
+ *   geometry     ICARUS_SPHERICAL or ICARUS_CARTESIAN (test problems).
+ *   x_min/x_max  r [AU], colatitude, longitude (x, y, z in Cartesian mode).
+ *   gamma, omega (rotation rate, normalised), cfl, divb_cd (cleaning
+ *                coefficient, 0 disables), p_floor, rho_floor.
+ *   precision    ICARUS_FP64 or ICARUS_FP32_MIXED (FP32 state and stencil,
+ *                FP64 pressure recovery in low-beta / thermally poor cells,
+ *                FP64 time-step reduction and conservation sums).
+ *   n_members    independent ensemble members sharing the grid geometry.
+ *   bc_lo/bc_hi  boundary kind per direction (ICARUS_BC_*); periodic must be
+ *                set on both sides; ICARUS_BC_INNER only at r low.
+ *   max_blocks   capacity of the block pool (all members); 0 = base blocks.
+ *   arena        caller-owned device memory, 256-byte aligned.
+ *   stream       cudaStream_t (NULL = legacy default stream). */
+typedef struct {
+  int n_cells[3];
+  int block[3];
+  int max_level;
+  int radial_stretch;
+  int geometry;
+  double x_min[3], x_max[3];
+  double gamma, omega, cfl, divb_cd;
+  double p_floor, rho_floor;
+  int precision;
+  int n_members;
+  int bc_lo[3], bc_hi[3];
+  int max_blocks;
+  void *arena;
+  size_t arena_bytes;
+  void *stream;
+} icarus_grid_desc;
+
+/* Cone CME (Eqs. 1-4): injected while t_start <= t <= t_start + t_max and the
+ * CME sphere still crosses the inner boundary.  colat/lon: launch direction in
+ * the co-rotating frame; half_width = omega_CME / 2; v = injection speed; rho,
+ * p: CME plasma (B = 0, radial flow). */
+typedef struct {
+  double t_start, t_max, colat, lon, half_width, v, rho, p;
+} icarus_cone;
+
+/* Refinement criterion: Loehner second-derivative estimator E of density and
+ * pressure (diagonal form, index space, noise parameter eps).  A block is
+ * flagged +1 (refine) if some interior cell has E > e_refine and
+ * v_r > v_r,background + dv; -1 (coarsen) if no cell has E > e_coarsen with
+ * that gate; 0 otherwise.  mode: ICARUS_FLAG_PLAIN, _LEARNED (MLP
+ * pre-flags OR plain flags), _BOTH (both computed, plain flags returned). */
+typedef struct {
+  double e_refine, e_coarsen, eps, dv;
+  int mode;
+} icarus_refine;
+
+/* Bytes of device arena that icarus_init_grid needs for this descriptor
+ * (arena/arena_bytes/stream fields are ignored). */
+icarus_status icarus_arena_bytes(const icarus_grid_desc *desc, size_t *bytes);
+
+/* Create a context on the caller's arena and stream: geometry tables for all
+ * levels, base-level blocks for every member, state zeroed.  *out receives
+ * the context (free with icarus_destroy). */
+icarus_status icarus_init_grid(const icarus_grid_desc *desc, icarus_ctx **out);
+
+/* Inner-boundary primitive map of one member (Sect. 2.1: boundary values
+ * constant in time in the co-rotating frame): host FP64 [8][n_theta][n_phi]
+ * at the base-level angular cells.  Both inner ghost layers of every level
+ * take the value of the containing base cell (not rescaled in r). */
+icarus_status icarus_set_inner_boundary(icarus_ctx *ctx, int member, const double *prim);
+
+/* Start a cone CME on one member (Eqs. 1-4) and record the member's
+ * background radial speed per base cell from the current state (the gate of
+ * the refinement criterion).  All leaves of the member must be at level 1. */
+icarus_status icarus_inject_cone_cme(icarus_ctx *ctx, int member, const icarus_cone *cme);
+
+/* Advance every member by up to n_steps steps of the midpoint
+ * predictor-corrector (each step: ghost fill, half step, ghost fill, full
+ * step with parabolic cleaning, reflux at coarse-fine faces, CFL time step).
+ * t_stop[n_members] (host): a member's dt is clipped so that it lands on
+ * t_stop, after which it stops.  t_out[n_members] (host, may be NULL)
+ * receives the members' times; passing it synchronises the stream. */
+icarus_status icarus_step(icarus_ctx *ctx, int n_steps, const double *t_stop, double *t_out);
+
+/* Evaluate the refinement criterion on every leaf of every member (after a
+ * ghost fill at the current time).  flags_out (host, optional): one int8 per
+ * leaf in global leaf order (member-major, Morton within a member). */
+icarus_status icarus_flag_refine(icarus_ctx *ctx, const icarus_refine *crit, int8_t *flags_out);
+
+/* Replace the current flags (host int8, global leaf order), e.g. to replay a
+ * decision taken elsewhere. */
+icarus_status icarus_set_flags(icarus_ctx *ctx, const int8_t *flags);
+
+/* Apply the current flags: refine +1 leaves by one level, coarsen complete
+ * sibling families all flagged -1 (refinement wins), enforce 2:1 balance over
+ * faces, edges and corners (least balanced refinement), prolong new children
+ * conservatively, restrict coarsened parents, renumber leaves in Morton order. */
+icarus_status icarus_regrid(icarus_ctx *ctx);
+
+/* Sample primitives at n_pts points rtp[n_pts][3] (host: r, colat, lon) by
+ * trilinear interpolation between cell centres of the finest leaf containing
+ * each point; prim_out[n_pts][8] (host).  Points outside the domain give NaN.
+ * Synchronises. */
+icarus_status icarus_probe(icarus_ctx *ctx, int member, int n_pts, const double *rtp, double *prim_out);
+
+/* ---- helpers used by the harness and the parity tests ---- */
+
+/* number of leaves of a member (member = -1: all members) */
+icarus_status icarus_n_leaves(icarus_ctx *ctx, int member, int *n);
+
+/* leaves of a member as rows (level, i, j, k), Morton order; host int32 [n][4] */
+icarus_status icarus_get_tree(icarus_ctx *ctx, int member, int32_t *rows, int capacity, int *n);
+
+/* Copy a member's state between host FP64 arrays and the device.
+ * is_prim = 1 takes primitive variables (converted on the device).  n = number
+ * of doubles in the host array (must equal leaves * 8 * cells per block). */
+icarus_status icarus_set_state(icarus_ctx *ctx, int member, const double *host, size_t n, int is_prim);
+icarus_status icarus_get_state(icarus_ctx *ctx, int member, double *host, size_t n);
+
+/* member time (host write / read) */
+icarus_status icarus_set_time(icarus_ctx *ctx, int member, double t);
+
+/* Per-member finest level (<= descriptor max_level). */
+icarus_status icarus_set_member_max_level(icarus_ctx *ctx, int member, int max_level);
+
+/* Fill ghost cells of the current state at the member times (the state the
+ * estimator and the probe see). */
+icarus_status icarus_ghost_fill(icarus_ctx *ctx);
+
+/* Deterministic FP64 sums over a member's leaves of V * U (8 doubles, host). */
+icarus_status icarus_conservation_sums(icarus_ctx *ctx, int member, double *out8);
+
+/* Current CFL time step of every member (host, n_members doubles). */
+icarus_status icarus_get_dt(icarus_ctx *ctx, double *dt_out);
+
+/* Sticky device status word: bit 0 NaN seen, bit 1 floor budget exceeded,
+ * bit 2 bounded wait gave up; *floor_hits receives the floor counter. */
+icarus_status icarus_status_word(icarus_ctx *ctx, uint32_t *word, uint64_t *floor_hits);
+
+/* Stage-kernel tile shape (theta x phi cells per CTA) and radial segment
+ * length; 0 = library default.  Used by the autotuner. */
+icarus_status icarus_set_tile(icarus_ctx *ctx, int tile_theta, int tile_phi, int r_segment);
+
+/* Capture one step of the launch sequence in a CUDA graph and replay it in
+ * icarus_step (1) or launch kernels directly (0).  Default 1. */
+icarus_status icarus_use_graph(icarus_ctx *ctx, int enable);
+
+/* Number of kernels launched per step with the current tree (for launch
+ * accounting). */
+icarus_status icarus_kernels_per_step(icarus_ctx *ctx, int *n);
+
+void icarus_destroy(icarus_ctx *ctx);
+const char *icarus_status_string(icarus_status s);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

@@ -1,0 +1,1283 @@
+// libicarus host runtime: the C ABI of include/icarus.h.
+//
+// Owns the small host-side bookkeeping of a context: the layout of the
+// caller's device arena, the per-level geometry tables (stretched radial
+// faces, Sect. 2.2 of arXiv 2211.12867), the leaf lists of every ensemble
+// member (block AMR of Sect. 3: factor 2 per level, neighbours within one
+// level), the regrid decision (2:1 balance over faces, edges and corners as
+// the least balanced refinement), the per-step launch sequence and its CUDA
+// graph.  All arithmetic on the state happens in the kernels.
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "../../include/icarus.h"
+#include "icarus_internal.h"
+
+namespace {
+
+constexpr size_t ALIGN = 256;
+
+struct Leaf {
+  int level;
+  int ix[3];
+};
+
+struct Member {
+  int max_level = 1;
+  std::vector<Leaf> leaves;            // Morton order
+  std::vector<std::vector<int>> map;   // per level: leaf index, -1 none/coarser, -2 refined
+  DevCme cme{};
+};
+
+struct Region {
+  size_t off = 0, bytes = 0;
+};
+
+struct Layout {
+  size_t total = 0;
+  Region geo, tables, blk, blk_alt, U, Us, Ualt, flux, lmap, lmap_off, bmap, cme, vbg, scal, flags, lists,
+      sides, rlist, ops, shell, staging, partial, probe_in, probe_out;
+  size_t staging_doubles = 0, table_doubles = 0;
+  int max_blocks = 0, nshell = 0;
+  long long lmap_ints = 0;
+  Region add(size_t b) {
+    Region r;
+    r.off = total;
+    r.bytes = b;
+    total += (b + ALIGN - 1) / ALIGN * ALIGN;
+    return r;
+  }
+};
+
+int nbase_total(const icarus_grid_desc *d) {
+  return (d->n_cells[0] / d->block[0]) * (d->n_cells[1] / d->block[1]) * (d->n_cells[2] / d->block[2]);
+}
+
+long long blocks_at_level(const icarus_grid_desc *d, int L) {
+  return (long long)nbase_total(d) << (3 * (L - 1));
+}
+
+// per level: r faces (N+2G+1) + 5 r cell tables (N+2G) + theta faces + 6
+// theta cell tables + phi faces + phi centres; then prolongation offsets
+size_t table_count(const icarus_grid_desc *d) {
+  size_t n = 0;
+  for (int L = 1; L <= d->max_level; L++) {
+    const size_t N0 = (size_t)d->n_cells[0] << (L - 1), N1 = (size_t)d->n_cells[1] << (L - 1),
+                 N2 = (size_t)d->n_cells[2] << (L - 1);
+    n += 2 * (N0 + 2 * NGH + 1) + 4 * (N0 + 2 * NGH);  // rf, r2f | dr3, dr2, rc, dr
+    n += 2 * (N1 + 2 * NGH + 1) + 5 * (N1 + 2 * NGH);  // tf, sinf | dcos, tc, sintc, costc, dth
+    n += (N2 + 2 * NGH + 1) + (N2 + 2 * NGH);          // pf | pc
+    if (L < d->max_level) n += 2 * (N0 + N1 + N2);     // offsets
+  }
+  return n;
+}
+
+int shell_count(const icarus_grid_desc *d) {
+  const int P = (d->block[0] + 2 * NGH) * (d->block[1] + 2 * NGH) * (d->block[2] + 2 * NGH);
+  return P - d->block[0] * d->block[1] * d->block[2];
+}
+
+icarus_status validate(const icarus_grid_desc *d) {
+  if (!d) return ICARUS_ERR_ARG;
+  if (d->max_level < 1 || d->max_level > MAXLEV) return ICARUS_ERR_ARG;
+  if (d->n_members < 1 || d->n_members > 4096) return ICARUS_ERR_ARG;
+  if (d->precision != ICARUS_FP64 && d->precision != ICARUS_FP32_MIXED) return ICARUS_ERR_ARG;
+  if (d->geometry != ICARUS_SPHERICAL && d->geometry != ICARUS_CARTESIAN) return ICARUS_ERR_ARG;
+  for (int k = 0; k < 3; k++) {
+    if (d->block[k] < 4 || d->block[k] % 2) return ICARUS_ERR_ARG;
+    if (d->n_cells[k] < d->block[k] || d->n_cells[k] % d->block[k]) return ICARUS_ERR_ARG;
+    if (!(d->x_max[k] > d->x_min[k])) return ICARUS_ERR_ARG;
+    if ((d->bc_lo[k] == ICARUS_BC_PERIODIC) != (d->bc_hi[k] == ICARUS_BC_PERIODIC)) return ICARUS_ERR_ARG;
+    if (d->bc_lo[k] < 0 || d->bc_lo[k] > 3 || d->bc_hi[k] < 0 || d->bc_hi[k] > 3) return ICARUS_ERR_ARG;
+    if (k > 0 && d->bc_lo[k] == ICARUS_BC_INNER) return ICARUS_ERR_ARG;
+    if (d->bc_hi[k] == ICARUS_BC_INNER) return ICARUS_ERR_ARG;
+    if (((long long)d->n_cells[k] << (d->max_level - 1)) > (1 << 20)) return ICARUS_ERR_ARG;
+  }
+  if (d->radial_stretch && !(d->x_min[0] > 0.0)) return ICARUS_ERR_ARG;
+  if (d->geometry == ICARUS_SPHERICAL && !(d->x_min[1] > 0.0 && d->x_max[1] < M_PI)) return ICARUS_ERR_ARG;
+  if (!(d->gamma > 1.0) || !(d->cfl > 0.0) || d->divb_cd < 0.0) return ICARUS_ERR_ARG;
+  if (d->max_blocks < 0) return ICARUS_ERR_ARG;
+  return ICARUS_OK;
+}
+
+Layout make_layout(const icarus_grid_desc *d) {
+  Layout L;
+  const int nm = d->n_members;
+  const int base = nbase_total(d) * nm;
+  L.max_blocks = d->max_blocks > 0 ? std::max(d->max_blocks, base) : base;
+  const size_t mb = L.max_blocks;
+  const size_t rs = d->precision == ICARUS_FP64 ? 8 : 4;
+  const size_t pc = (size_t)(d->block[0] + 2 * NGH) * (d->block[1] + 2 * NGH) * (d->block[2] + 2 * NGH);
+  const size_t ic = (size_t)d->block[0] * d->block[1] * d->block[2];
+  const bool amr = d->max_level > 1;
+  L.table_doubles = table_count(d);
+  L.geo = L.add(sizeof(Geometry));
+  L.tables = L.add(L.table_doubles * (8 + 4));
+  L.blk = L.add(mb * sizeof(DevBlock));
+  L.blk_alt = L.add(amr ? mb * sizeof(DevBlock) : 0);
+  L.U = L.add(mb * NVAR * pc * rs);
+  L.Us = L.add(mb * NVAR * pc * rs);
+  L.Ualt = L.add(amr ? mb * NVAR * pc * rs : 0);
+  const size_t fcells = 2 * ((size_t)d->block[1] * d->block[2] + (size_t)d->block[0] * d->block[2] +
+                             (size_t)d->block[0] * d->block[1]);
+  L.flux = L.add(amr ? mb * NVAR * fcells * rs : 0);
+  long long li = 0;
+  for (int Lv = 1; Lv <= d->max_level; Lv++) li += blocks_at_level(d, Lv);
+  L.lmap_ints = li * nm;
+  L.lmap = L.add((size_t)L.lmap_ints * sizeof(int));
+  L.lmap_off = L.add((size_t)nm * (MAXLEV + 1) * sizeof(long long));
+  L.bmap = L.add((size_t)nm * NVAR * d->n_cells[1] * d->n_cells[2] * sizeof(double));
+  L.cme = L.add((size_t)nm * sizeof(DevCme));
+  L.vbg = L.add((size_t)nm * d->n_cells[0] * d->n_cells[1] * d->n_cells[2] * sizeof(double));
+  L.scal = L.add((size_t)nm * 5 * sizeof(double) + 64);
+  L.flags = L.add(mb);
+  L.lists = L.add(2 * mb * sizeof(int));        // all-leaf list + per-level lists
+  L.sides = L.add(6 * mb * sizeof(int2));       // (slot, side) per level, per direction
+  L.rlist = L.add(mb * sizeof(int));
+  L.ops = L.add(amr ? mb * sizeof(MoveOp) : 0);
+  L.nshell = shell_count(d);
+  L.shell = L.add((size_t)L.nshell * sizeof(int));
+  const size_t per_block = NVAR * ic;
+  size_t chunk = std::max<size_t>(1, (size_t)(64u << 20) / (per_block * 8));
+  chunk = std::min(chunk, mb);
+  L.staging_doubles = chunk * per_block;
+  L.staging = L.add(L.staging_doubles * sizeof(double));
+  L.partial = L.add(mb * NVAR * sizeof(double));
+  L.probe_in = L.add(4096 * 3 * sizeof(double));
+  L.probe_out = L.add(4096 * NVAR * sizeof(double));
+  return L;
+}
+
+// 8-point Gauss-Legendre rule on [-1, 1] (Newton iteration on P_8)
+void gauss_legendre(double *x, double *w) {
+  const int n = 8;
+  for (int i = 0; i < n; i++) {
+    double z = std::cos(M_PI * (i + 0.75) / (n + 0.5));
+    for (int it = 0; it < 100; it++) {
+      double p0 = 1.0, p1 = z;
+      for (int k = 2; k <= n; k++) {
+        double p2 = ((2 * k - 1) * z * p1 - (k - 1) * p0) / k;
+        p0 = p1;
+        p1 = p2;
+      }
+      double dp = n * (z * p1 - p0) / (z * z - 1.0);
+      double dz = p1 / dp;
+      z -= dz;
+      if (std::fabs(dz) < 1e-16) break;
+    }
+    double p0 = 1.0, p1 = z;
+    for (int k = 2; k <= n; k++) {
+      double p2 = ((2 * k - 1) * z * p1 - (k - 1) * p0) / k;
+      p0 = p1;
+      p1 = p2;
+    }
+    double dp = n * (z * p1 - p0) / (z * z - 1.0);
+    x[i] = z;
+    w[i] = 2.0 / ((1.0 - z * z) * dp * dp);
+  }
+}
+
+}  // namespace
+
+struct icarus_ctx {
+  icarus_grid_desc d{};
+  Layout lay;
+  int prec = 0;
+  size_t rsize = 8;
+  cudaStream_t stream = nullptr;
+  char *arena = nullptr;
+  int nsm = 1;
+  // device pointers
+  Geometry *geo = nullptr;
+  DevBlock *blk = nullptr, *blk_alt = nullptr;
+  void *U = nullptr, *Us = nullptr, *Ualt = nullptr, *flux = nullptr;
+  int *lmap = nullptr;
+  long long *lmap_off = nullptr;
+  double *bmap = nullptr, *vbg = nullptr, *staging = nullptr, *partial = nullptr, *probe_in = nullptr,
+         *probe_out = nullptr;
+  DevCme *cme = nullptr;
+  double *t = nullptr, *dt_used = nullptr, *dt_cfl = nullptr, *tstop = nullptr;
+  unsigned long long *inv_max = nullptr, *floor_hits = nullptr;
+  unsigned int *status = nullptr;
+  signed char *flags = nullptr;
+  int *all_list = nullptr, *lvl_list = nullptr, *rlist = nullptr, *shell = nullptr;
+  int2 *sides = nullptr;
+  MoveOp *ops = nullptr;
+  // host mirrors
+  std::vector<Member> mem;
+  int nleaves = 0;
+  std::vector<int> mem_off;                 // first slot of each member
+  std::vector<DevBlock> hblk;
+  int lvl_count[MAXLEV + 1] = {0}, lvl_start[MAXLEV + 1] = {0};
+  int side_count[MAXLEV + 1][3] = {{0}}, side_start[MAXLEV + 1][3] = {{0}};
+  int nrlist = 0, max_level_present = 1;
+  std::vector<signed char> hflags;
+  bool flags_valid = false;
+  KParams kp{};
+  // launch configuration
+  int tile_j = 0, tile_k = 0, seg_len = 0, occ = 1;
+  bool use_graph = true;
+  cudaGraphExec_t graph = nullptr;
+  bool graph_valid = false;
+  bool poisoned = false;
+  std::vector<double> h_tstop;
+  int kernels_per_step = 0;
+};
+
+namespace {
+
+#define CK(x)                                                                     \
+  do {                                                                            \
+    cudaError_t e_ = (x);                                                         \
+    if (e_ != cudaSuccess) {                                                      \
+      fprintf(stderr, "libicarus: %s failed: %s\n", #x, cudaGetErrorString(e_)); \
+      return ICARUS_ERR_CUDA;                                                     \
+    }                                                                             \
+  } while (0)
+
+template <typename T>
+T *at(icarus_ctx *c, const Region &r) {
+  return reinterpret_cast<T *>(c->arena + r.off);
+}
+
+uint64_t morton_key(const Leaf &l, int shift_to) {
+  uint64_t key = 0;
+  const int s = shift_to - l.level;
+  uint64_t x[3];
+  for (int d = 0; d < 3; d++) x[d] = (uint64_t)l.ix[d] << s;
+  for (int bit = 20; bit >= 0; bit--)
+    for (int d = 0; d < 3; d++) key = (key << 1) | ((x[d] >> bit) & 1u);
+  return key;
+}
+
+int nblk_dim(const icarus_ctx *c, int L, int d) { return (c->d.n_cells[d] / c->d.block[d]) << (L - 1); }
+
+long long map_index(const icarus_ctx *c, int L, const int *b) {
+  return ((long long)b[0] * nblk_dim(c, L, 1) + b[1]) * nblk_dim(c, L, 2) + b[2];
+}
+
+// wrap a block index of level L; false if outside a non-periodic direction
+bool wrap_block(const icarus_ctx *c, int L, int *b) {
+  for (int d = 0; d < 3; d++) {
+    const int n = nblk_dim(c, L, d);
+    if (c->d.bc_lo[d] == ICARUS_BC_PERIODIC) {
+      b[d] = ((b[d] % n) + n) % n;
+    } else if (b[d] < 0 || b[d] >= n) {
+      return false;
+    }
+  }
+  return true;
+}
+
+void build_member_map(icarus_ctx *c, Member &m) {
+  m.map.assign(c->d.max_level + 1, std::vector<int>());
+  for (int L = 1; L <= c->d.max_level; L++) m.map[L].assign((size_t)blocks_at_level(&c->d, L), -1);
+  for (size_t n = 0; n < m.leaves.size(); n++) {
+    const Leaf &l = m.leaves[n];
+    m.map[l.level][map_index(c, l.level, l.ix)] = (int)n;
+    int b[3] = {l.ix[0], l.ix[1], l.ix[2]};
+    for (int L = l.level - 1; L >= 1; L--) {
+      for (int d = 0; d < 3; d++) b[d] >>= 1;
+      m.map[L][map_index(c, L, b)] = -2;
+    }
+  }
+}
+
+// relation of the region (level L, block index b) to the leaves: the leaf
+// index, -2 refined, -1 covered by a coarser leaf
+int region_state(const icarus_ctx *c, const Member &m, int L, const int *b) { return m.map[L][map_index(c, L, b)]; }
+
+// adjacent leaves of leaf n (faces, edges, corners)
+void neighbours(const icarus_ctx *c, const Member &m, int n, std::vector<int> &out) {
+  out.clear();
+  const Leaf &l = m.leaves[n];
+  const int L = l.level;
+  for (int dx = -1; dx <= 1; dx++)
+    for (int dy = -1; dy <= 1; dy++)
+      for (int dz = -1; dz <= 1; dz++) {
+        if (!dx && !dy && !dz) continue;
+        const int dir[3] = {dx, dy, dz};
+        int b[3] = {l.ix[0] + dx, l.ix[1] + dy, l.ix[2] + dz};
+        if (!wrap_block(c, L, b)) continue;
+        const int s = region_state(c, m, L, b);
+        if (s >= 0) {
+          out.push_back(s);
+        } else if (s == -2) {
+          if (L + 1 > c->d.max_level) continue;
+          for (int ch = 0; ch < 8; ch++) {
+            const int o[3] = {(ch >> 2) & 1, (ch >> 1) & 1, ch & 1};
+            bool touch = true;
+            for (int d = 0; d < 3; d++) {
+              if (dir[d] == 1 && o[d] != 0) touch = false;
+              if (dir[d] == -1 && o[d] != 1) touch = false;
+            }
+            if (!touch) continue;
+            int cb[3];
+            for (int d = 0; d < 3; d++) cb[d] = 2 * b[d] + o[d];
+            const int cs = region_state(c, m, L + 1, cb);
+            if (cs >= 0) out.push_back(cs);
+          }
+        } else {
+          int pb[3] = {b[0] >> 1, b[1] >> 1, b[2] >> 1};
+          if (L > 1) {
+            const int ps = region_state(c, m, L - 1, pb);
+            if (ps >= 0) out.push_back(ps);
+          }
+        }
+      }
+  std::sort(out.begin(), out.end());
+  out.erase(std::unique(out.begin(), out.end()), out.end());
+}
+
+// device tables that depend on the leaf lists
+icarus_status upload_tree(icarus_ctx *c, DevBlock *blk_dst) {
+  const icarus_grid_desc &d = c->d;
+  c->nleaves = 0;
+  c->mem_off.assign(d.n_members, 0);
+  for (int m = 0; m < d.n_members; m++) {
+    c->mem_off[m] = c->nleaves;
+    c->nleaves += (int)c->mem[m].leaves.size();
+  }
+  if (c->nleaves > c->lay.max_blocks) return ICARUS_ERR_CAPACITY;
+  c->hblk.assign(c->nleaves, DevBlock{});
+  std::vector<int> all(c->nleaves);
+  std::vector<std::vector<int>> per_level(MAXLEV + 1);
+  std::vector<std::vector<int2>> sd[3];
+  for (int k = 0; k < 3; k++) sd[k].assign(MAXLEV + 1, std::vector<int2>());
+  std::vector<int> rl;
+  c->max_level_present = 1;
+  for (int m = 0; m < d.n_members; m++) {
+    const Member &M = c->mem[m];
+    for (size_t n = 0; n < M.leaves.size(); n++) {
+      const Leaf &l = M.leaves[n];
+      const int slot = c->mem_off[m] + (int)n;
+      DevBlock &B = c->hblk[slot];
+      B.member = m;
+      B.level = l.level;
+      for (int k = 0; k < 3; k++) B.ix[k] = l.ix[k];
+      B.phys = 0;
+      bool finer = false;
+      for (int f = 0; f < 6; f++) {
+        const int dd = f / 2, hi = f % 2;
+        int b[3] = {l.ix[0], l.ix[1], l.ix[2]};
+        b[dd] += hi ? 1 : -1;
+        if (!wrap_block(c, l.level, b)) {
+          B.nbr[f] = NB_PHYS;
+          B.phys |= 1 << f;
+          sd[dd][l.level].push_back(make_int2(slot, hi));
+          continue;
+        }
+        const int s = region_state(c, M, l.level, b);
+        B.nbr[f] = s >= 0 ? NB_SAME : (s == -2 ? NB_FINER : NB_COARSER);
+        if (s == -2) finer = true;
+      }
+      if (finer) rl.push_back(slot);
+      all[slot] = slot;
+      per_level[l.level].push_back(slot);
+      c->max_level_present = std::max(c->max_level_present, l.level);
+    }
+  }
+  // level maps (slot numbers)
+  std::vector<int> lm((size_t)c->lay.lmap_ints, -1);
+  std::vector<long long> off((size_t)d.n_members * (MAXLEV + 1), 0);
+  long long o = 0;
+  for (int m = 0; m < d.n_members; m++)
+    for (int L = 1; L <= d.max_level; L++) {
+      off[(size_t)m * (MAXLEV + 1) + L] = o;
+      const std::vector<int> &mp = c->mem[m].map[L];
+      for (size_t q = 0; q < mp.size(); q++) lm[o + q] = mp[q] >= 0 ? mp[q] + c->mem_off[m] : mp[q];
+      o += (long long)mp.size();
+    }
+  std::vector<int> lv;
+  for (int L = 1; L <= MAXLEV; L++) {
+    c->lvl_start[L] = (int)lv.size();
+    c->lvl_count[L] = (int)per_level[L].size();
+    lv.insert(lv.end(), per_level[L].begin(), per_level[L].end());
+  }
+  std::vector<int2> sv;
+  for (int L = 1; L <= MAXLEV; L++)
+    for (int k = 0; k < 3; k++) {
+      c->side_start[L][k] = (int)sv.size();
+      c->side_count[L][k] = (int)sd[k][L].size();
+      sv.insert(sv.end(), sd[k][L].begin(), sd[k][L].end());
+    }
+  c->nrlist = (int)rl.size();
+  cudaStream_t s = c->stream;
+  CK(cudaMemcpyAsync(blk_dst, c->hblk.data(), sizeof(DevBlock) * c->nleaves, cudaMemcpyHostToDevice, s));
+  CK(cudaMemcpyAsync(c->lmap, lm.data(), sizeof(int) * lm.size(), cudaMemcpyHostToDevice, s));
+  CK(cudaMemcpyAsync(c->lmap_off, off.data(), sizeof(long long) * off.size(), cudaMemcpyHostToDevice, s));
+  CK(cudaMemcpyAsync(c->all_list, all.data(), sizeof(int) * all.size(), cudaMemcpyHostToDevice, s));
+  CK(cudaMemcpyAsync(c->lvl_list, lv.data(), sizeof(int) * lv.size(), cudaMemcpyHostToDevice, s));
+  if (!sv.empty()) CK(cudaMemcpyAsync(c->sides, sv.data(), sizeof(int2) * sv.size(), cudaMemcpyHostToDevice, s));
+  if (!rl.empty()) CK(cudaMemcpyAsync(c->rlist, rl.data(), sizeof(int) * rl.size(), cudaMemcpyHostToDevice, s));
+  // host buffers above are freed on return: wait for the copies
+  CK(cudaStreamSynchronize(s));
+  c->graph_valid = false;
+  c->flags_valid = false;
+  return ICARUS_OK;
+}
+
+void fill_kp(icarus_ctx *c) {
+  KParams &k = c->kp;
+  const icarus_grid_desc &d = c->d;
+  for (int i = 0; i < 3; i++) {
+    k.nb[i] = d.block[i];
+    k.P[i] = d.block[i] + 2 * NGH;
+    k.nbase[i] = d.n_cells[i] / d.block[i];
+    k.bc_lo[i] = d.bc_lo[i];
+    k.bc_hi[i] = d.bc_hi[i];
+    k.n_base_cells[i] = d.n_cells[i];
+  }
+  k.pcells = k.P[0] * k.P[1] * k.P[2];
+  k.icells = k.nb[0] * k.nb[1] * k.nb[2];
+  k.n_members = d.n_members;
+  k.geometry = d.geometry;
+  k.gamma = d.gamma;
+  k.omega = d.omega;
+  k.cd = d.divb_cd;
+  k.p_floor = d.p_floor;
+  k.rho_floor = d.rho_floor;
+  k.geo = c->geo;
+  k.blk = c->blk;
+  k.lmap = c->lmap;
+  k.lmap_off = c->lmap_off;
+  k.bmap = c->bmap;
+  k.cme = c->cme;
+  k.vbg = c->vbg;
+  k.t = c->t;
+  k.dt_used = c->dt_used;
+  k.dt_cfl = c->dt_cfl;
+  k.inv_max = c->inv_max;
+  k.status = c->status;
+  k.floor_hits = c->floor_hits;
+}
+
+// geometry tables of every level, FP64 and FP32 copies
+icarus_status build_geometry(icarus_ctx *c) {
+  const icarus_grid_desc &d = c->d;
+  std::vector<double> hd;
+  hd.reserve(c->lay.table_doubles);
+  Geometry hg;
+  memset(&hg, 0, sizeof(hg));
+  double *dbase = at<double>(c, c->lay.tables);
+  float *fbase = reinterpret_cast<float *>(dbase + c->lay.table_doubles);
+  struct Rec {
+    size_t off;
+    int lev, which, dir;
+  };
+  std::vector<Rec> recs;
+  auto push = [&](const std::vector<double> &v) {
+    size_t o = hd.size();
+    hd.insert(hd.end(), v.begin(), v.end());
+    return o;
+  };
+  const bool sph = d.geometry == ICARUS_SPHERICAL;
+  auto face = [&](int L, int dd, int I) {
+    const int N = d.n_cells[dd] << (L - 1);
+    const double x = (double)I / (double)N;
+    if (dd == 0 && sph && d.radial_stretch) return d.x_min[0] * std::pow(d.x_max[0] / d.x_min[0], x);
+    return d.x_min[dd] + (d.x_max[dd] - d.x_min[dd]) * x;
+  };
+  std::vector<size_t> offs[MAXLEV + 1];
+  for (int L = 1; L <= d.max_level; L++) {
+    const int N0 = d.n_cells[0] << (L - 1), N1 = d.n_cells[1] << (L - 1), N2 = d.n_cells[2] << (L - 1);
+    std::vector<double> rf(N0 + 2 * NGH + 1), r2f(rf.size()), dr3(N0 + 2 * NGH), dr2(dr3.size()), rc(dr3.size()),
+        dr(dr3.size());
+    for (int I = -NGH; I <= N0 + NGH; I++) {
+      rf[I + NGH] = face(L, 0, I);
+      r2f[I + NGH] = sph ? rf[I + NGH] * rf[I + NGH] : 1.0;
+    }
+    for (int I = -NGH; I < N0 + NGH; I++) {
+      const double a = rf[I + NGH], b = rf[I + NGH + 1];
+      dr3[I + NGH] = sph ? (b * b * b - a * a * a) / 3.0 : b - a;
+      dr2[I + NGH] = sph ? (b * b - a * a) / 2.0 : b - a;
+      rc[I + NGH] = 0.5 * (a + b);
+      dr[I + NGH] = b - a;
+    }
+    std::vector<double> tf(N1 + 2 * NGH + 1), sinf(tf.size()), dcos(N1 + 2 * NGH), tc(dcos.size()), sintc(dcos.size()),
+        costc(dcos.size()), dth(dcos.size());
+    for (int J = -NGH; J <= N1 + NGH; J++) {
+      tf[J + NGH] = face(L, 1, J);
+      sinf[J + NGH] = sph ? std::sin(tf[J + NGH]) : 1.0;
+    }
+    for (int J = -NGH; J < N1 + NGH; J++) {
+      const double a = tf[J + NGH], b = tf[J + NGH + 1];
+      dcos[J + NGH] = sph ? std::cos(a) - std::cos(b) : b - a;
+      tc[J + NGH] = 0.5 * (a + b);
+      sintc[J + NGH] = sph ? std::sin(tc[J + NGH]) : 1.0;
+      costc[J + NGH] = sph ? std::cos(tc[J + NGH]) : 0.0;
+      dth[J + NGH] = b - a;
+    }
+    std::vector<double> pf(N2 + 2 * NGH + 1), pcv(N2 + 2 * NGH);
+    for (int K = -NGH; K <= N2 + NGH; K++) pf[K + NGH] = face(L, 2, K);
+    for (int K = -NGH; K < N2 + NGH; K++) pcv[K + NGH] = 0.5 * (pf[K + NGH] + pf[K + NGH + 1]);
+    const double dphi = (d.x_max[2] - d.x_min[2]) / N2;
+    std::vector<size_t> &o = offs[L];
+    o.push_back(push(rf));
+    o.push_back(push(r2f));
+    o.push_back(push(dr3));
+    o.push_back(push(dr2));
+    o.push_back(push(rc));
+    o.push_back(push(dr));
+    o.push_back(push(tf));
+    o.push_back(push(sinf));
+    o.push_back(push(dcos));
+    o.push_back(push(tc));
+    o.push_back(push(sintc));
+    o.push_back(push(costc));
+    o.push_back(push(dth));
+    o.push_back(push(pf));
+    o.push_back(push(pcv));
+    hg.d[L].dphi = dphi;
+    hg.f[L].dphi = (float)dphi;
+    hg.d[L].n[0] = hg.f[L].n[0] = N0;
+    hg.d[L].n[1] = hg.f[L].n[1] = N1;
+    hg.d[L].n[2] = hg.f[L].n[2] = N2;
+  }
+  // prolongation offsets: child centroid minus parent centroid in the
+  // parent's index coordinate, volume weighted (8-point Gauss-Legendre on
+  // each child; exact for the polynomial weights)
+  double gx[8], gw[8];
+  gauss_legendre(gx, gw);
+  for (int L = 1; L < d.max_level; L++) {
+    for (int dd = 0; dd < 3; dd++) {
+      const int N = d.n_cells[dd] << (L - 1);
+      std::vector<double> t(2 * (size_t)N);
+      const bool logr = sph && dd == 0 && d.radial_stretch;
+      for (int I = 0; I < N; I++) {
+        const double a = face(L, dd, I), b = face(L, dd, I + 1), m = face(L + 1, dd, 2 * I + 1);
+        auto weight = [&](double x) {
+          if (!sph || dd == 2) return 1.0;
+          return dd == 0 ? x * x : std::sin(x);
+        };
+        auto xi = [&](double x) { return logr ? std::log(x / a) / std::log(b / a) - 0.5 : (x - a) / (b - a) - 0.5; };
+        double M0[2], M1[2];
+        for (int ch = 0; ch < 2; ch++) {
+          const double lo = ch ? m : a, hi = ch ? b : m, h = 0.5 * (hi - lo), mid = 0.5 * (hi + lo);
+          M0[ch] = M1[ch] = 0.0;
+          for (int q = 0; q < 8; q++) {
+            const double x = mid + h * gx[q];
+            const double wv = gw[q] * h * weight(x);
+            M0[ch] += wv;
+            M1[ch] += wv * xi(x);
+          }
+        }
+        const double xp = (M1[0] + M1[1]) / (M0[0] + M0[1]);
+        t[2 * I] = M1[0] / M0[0] - xp;
+        t[2 * I + 1] = M1[1] / M0[1] - xp;
+      }
+      offs[L].push_back(push(t));
+    }
+  }
+  if (hd.size() != c->lay.table_doubles) {
+    fprintf(stderr, "libicarus: geometry table size mismatch\n");
+    return ICARUS_ERR_ARG;
+  }
+  std::vector<float> hf(hd.size());
+  for (size_t i = 0; i < hd.size(); i++) hf[i] = (float)hd[i];
+  for (int L = 1; L <= d.max_level; L++) {
+    const std::vector<size_t> &o = offs[L];
+    const double *b = dbase;
+    const float *f = fbase;
+    LevelGeo<double> &G = hg.d[L];
+    LevelGeo<float> &F = hg.f[L];
+    G.rf = b + o[0]; F.rf = f + o[0];
+    G.r2f = b + o[1]; F.r2f = f + o[1];
+    G.dr3 = b + o[2]; F.dr3 = f + o[2];
+    G.dr2 = b + o[3]; F.dr2 = f + o[3];
+    G.rc = b + o[4]; F.rc = f + o[4];
+    G.dr = b + o[5]; F.dr = f + o[5];
+    G.tf = b + o[6]; F.tf = f + o[6];
+    G.sinf = b + o[7]; F.sinf = f + o[7];
+    G.dcos = b + o[8]; F.dcos = f + o[8];
+    G.tc = b + o[9]; F.tc = f + o[9];
+    G.sintc = b + o[10]; F.sintc = f + o[10];
+    G.costc = b + o[11]; F.costc = f + o[11];
+    G.dth = b + o[12]; F.dth = f + o[12];
+    G.pf = b + o[13]; F.pf = f + o[13];
+    G.pc = b + o[14]; F.pc = f + o[14];
+    if (L < d.max_level)
+      for (int dd = 0; dd < 3; dd++) {
+        hg.dlt[L][dd] = b + o[15 + dd];
+        hg.dltf[L][dd] = f + o[15 + dd];
+      }
+  }
+  CK(cudaMemcpyAsync(dbase, hd.data(), sizeof(double) * hd.size(), cudaMemcpyHostToDevice, c->stream));
+  CK(cudaMemcpyAsync(fbase, hf.data(), sizeof(float) * hf.size(), cudaMemcpyHostToDevice, c->stream));
+  CK(cudaMemcpyAsync(c->geo, &hg, sizeof(Geometry), cudaMemcpyHostToDevice, c->stream));
+  CK(cudaStreamSynchronize(c->stream));
+  return ICARUS_OK;
+}
+
+// ---- launch sequence ----
+void default_tiles(icarus_ctx *c) {
+  const int n1 = c->d.block[1], n2 = c->d.block[2];
+  if (c->tile_j && c->tile_k) {
+    c->occ = stage_max_ctas_per_sm(c->prec, c->tile_j, c->tile_k);
+    return;
+  }
+  if (n2 >= 32) {
+    c->tile_j = c->prec ? 8 : 4;
+    c->tile_k = 32;
+  } else if (n1 >= 12 && n2 >= 12) {
+    c->tile_j = 12;
+    c->tile_k = 12;
+  } else {
+    c->tile_j = 8;
+    c->tile_k = 8;
+  }
+  c->occ = stage_max_ctas_per_sm(c->prec, c->tile_j, c->tile_k);
+}
+
+StageLaunch stage_cfg(icarus_ctx *c, int stage2) {
+  StageLaunch sl{};
+  sl.tile_j = c->tile_j;
+  sl.tile_k = c->tile_k;
+  sl.tiles_j = (c->d.block[1] + sl.tile_j - 1) / sl.tile_j;
+  sl.tiles_k = (c->d.block[2] + sl.tile_k - 1) / sl.tile_k;
+  const int slots = c->nsm * c->occ;
+  int seg = c->seg_len;
+  if (seg <= 0) {
+    // enough work items for ~4 waves of the persistent grid, segments >= 8 planes
+    const long long base = (long long)c->nleaves * sl.tiles_j * sl.tiles_k;
+    long long segs = (4LL * slots + base - 1) / std::max(1LL, base);
+    segs = std::max(1LL, std::min<long long>(segs, c->d.block[0] / 8 > 0 ? c->d.block[0] / 8 : 1));
+    seg = (c->d.block[0] + (int)segs - 1) / (int)segs;
+  }
+  seg = std::max(1, std::min(seg, c->d.block[0]));
+  sl.seg_len = seg;
+  sl.segs = (c->d.block[0] + seg - 1) / seg;
+  sl.list = c->all_list;
+  sl.nlist = c->nleaves;
+  const long long nwork = (long long)sl.nlist * sl.tiles_j * sl.tiles_k * sl.segs;
+  sl.grid = (int)std::max(1LL, std::min<long long>(nwork, slots));
+  sl.stage2 = stage2;
+  sl.dtfac = stage2 ? 1.0 : 0.5;
+  return sl;
+}
+
+int enqueue_ghost(icarus_ctx *c, void *buf, double tfac) {
+  int n = 0;
+  for (int L = 1; L <= c->max_level_present; L++) {
+    if (c->lvl_count[L] == 0) continue;
+    ghost_neighbour_launch(c->kp, buf, c->prec, c->lvl_list + c->lvl_start[L], c->lvl_count[L], c->shell,
+                           c->lay.nshell, L, c->stream);
+    n++;
+    for (int dd = 0; dd < 3; dd++) {
+      if (c->side_count[L][dd] == 0) continue;
+      ghost_physical_launch(c->kp, buf, c->prec, c->sides + c->side_start[L][dd], c->side_count[L][dd], dd, L, tfac,
+                            c->stream);
+      n++;
+    }
+  }
+  return n;
+}
+
+int enqueue_step(icarus_ctx *c) {
+  int n = 0;
+  dt_begin_launch(c->kp, c->tstop, c->stream);
+  n++;
+  n += enqueue_ghost(c, c->U, 0.0);
+  StageLaunch s1 = stage_cfg(c, 0);
+  s1.Uin = c->U;
+  s1.U0 = c->U;
+  s1.Uout = c->Us;
+  s1.flux = nullptr;
+  stage_launch(c->kp, s1, c->prec, c->stream);
+  n++;
+  n += enqueue_ghost(c, c->Us, 0.5);
+  StageLaunch s2 = stage_cfg(c, 1);
+  s2.Uin = c->Us;
+  s2.U0 = c->U;
+  s2.Uout = c->U;
+  s2.flux = c->d.max_level > 1 ? c->flux : nullptr;
+  stage_launch(c->kp, s2, c->prec, c->stream);
+  n++;
+  if (c->nrlist > 0) {
+    reflux_launch(c->kp, c->U, c->flux, c->prec, c->rlist, c->nrlist, c->stream);
+    n++;
+  }
+  dt_finalize_launch(c->kp, c->d.cfl, c->stream);
+  n++;
+  return n;
+}
+
+icarus_status check_status(icarus_ctx *c) {
+  unsigned int w = 0;
+  CK(cudaMemcpyAsync(&w, c->status, sizeof(w), cudaMemcpyDeviceToHost, c->stream));
+  CK(cudaStreamSynchronize(c->stream));
+  if (w & ST_NAN) {
+    c->poisoned = true;
+    return ICARUS_ERR_NONPHYSICAL;
+  }
+  if (w & ST_TIMEOUT) {
+    c->poisoned = true;
+    return ICARUS_ERR_TIMEOUT;
+  }
+  return ICARUS_OK;
+}
+
+icarus_status recompute_dt(icarus_ctx *c) {
+  CK(cudaMemsetAsync(c->inv_max, 0, sizeof(unsigned long long) * c->d.n_members, c->stream));
+  dt_full_launch(c->kp, c->U, c->prec, c->nleaves, c->d.cfl, c->stream);
+  CK(cudaPeekAtLastError());
+  return ICARUS_OK;
+}
+
+bool member_ok(icarus_ctx *c, int m) { return c && m >= 0 && m < c->d.n_members; }
+
+}  // namespace
+
+// ======================================================================
+extern "C" {
+
+const char *icarus_status_string(icarus_status s) {
+  switch (s) {
+    case ICARUS_OK: return "ok";
+    case ICARUS_ERR_ARG: return "invalid argument";
+    case ICARUS_ERR_ARENA: return "arena too small or misaligned";
+    case ICARUS_ERR_CUDA: return "CUDA runtime error";
+    case ICARUS_ERR_NONPHYSICAL: return "non-physical state on the device";
+    case ICARUS_ERR_TIMEOUT: return "bounded device wait gave up";
+    case ICARUS_ERR_STATE: return "call out of order or context poisoned";
+    case ICARUS_ERR_CAPACITY: return "block pool capacity exceeded";
+  }
+  return "unknown status";
+}
+
+icarus_status icarus_arena_bytes(const icarus_grid_desc *desc, size_t *bytes) {
+  if (!bytes) return ICARUS_ERR_ARG;
+  icarus_status st = validate(desc);
+  if (st != ICARUS_OK) return st;
+  *bytes = make_layout(desc).total;
+  return ICARUS_OK;
+}
+
+icarus_status icarus_init_grid(const icarus_grid_desc *desc, icarus_ctx **out) {
+  if (!out) return ICARUS_ERR_ARG;
+  *out = nullptr;
+  icarus_status st = validate(desc);
+  if (st != ICARUS_OK) return st;
+  Layout lay = make_layout(desc);
+  if (!desc->arena || desc->arena_bytes < lay.total) return ICARUS_ERR_ARENA;
+  if ((uintptr_t)desc->arena % ALIGN) return ICARUS_ERR_ARENA;
+  icarus_ctx *c = new (std::nothrow) icarus_ctx();
+  if (!c) return ICARUS_ERR_ARG;
+  c->d = *desc;
+  c->lay = lay;
+  c->prec = desc->precision == ICARUS_FP32_MIXED ? 1 : 0;
+  c->rsize = c->prec ? 4 : 8;
+  c->stream = (cudaStream_t)desc->stream;
+  c->arena = (char *)desc->arena;
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess ||
+      cudaDeviceGetAttribute(&c->nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) {
+    delete c;
+    return ICARUS_ERR_CUDA;
+  }
+  c->geo = at<Geometry>(c, lay.geo);
+  c->blk = at<DevBlock>(c, lay.blk);
+  c->blk_alt = lay.blk_alt.bytes ? at<DevBlock>(c, lay.blk_alt) : nullptr;
+  c->U = c->arena + lay.U.off;
+  c->Us = c->arena + lay.Us.off;
+  c->Ualt = lay.Ualt.bytes ? c->arena + lay.Ualt.off : nullptr;
+  c->flux = lay.flux.bytes ? c->arena + lay.flux.off : nullptr;
+  c->lmap = at<int>(c, lay.lmap);
+  c->lmap_off = at<long long>(c, lay.lmap_off);
+  c->bmap = at<double>(c, lay.bmap);
+  c->cme = at<DevCme>(c, lay.cme);
+  c->vbg = at<double>(c, lay.vbg);
+  double *sc = at<double>(c, lay.scal);
+  const int nm = desc->n_members;
+  c->t = sc;
+  c->dt_used = sc + nm;
+  c->dt_cfl = sc + 2 * nm;
+  c->tstop = sc + 3 * nm;
+  c->inv_max = reinterpret_cast<unsigned long long *>(sc + 4 * nm);
+  c->status = reinterpret_cast<unsigned int *>(sc + 5 * nm);
+  c->floor_hits = reinterpret_cast<unsigned long long *>(sc + 5 * nm + 1);
+  c->flags = at<signed char>(c, lay.flags);
+  c->all_list = at<int>(c, lay.lists);
+  c->lvl_list = c->all_list + lay.max_blocks;
+  c->sides = at<int2>(c, lay.sides);
+  c->rlist = at<int>(c, lay.rlist);
+  c->ops = lay.ops.bytes ? at<MoveOp>(c, lay.ops) : nullptr;
+  c->shell = at<int>(c, lay.shell);
+  c->staging = at<double>(c, lay.staging);
+  c->partial = at<double>(c, lay.partial);
+  c->probe_in = at<double>(c, lay.probe_in);
+  c->probe_out = at<double>(c, lay.probe_out);
+  auto fail = [&](icarus_status s) {
+    delete c;
+    return s;
+  };
+  // zero the small per-member and status words; the state pools are zeroed too
+  if (cudaMemsetAsync(c->arena + lay.scal.off, 0, lay.scal.bytes, c->stream) != cudaSuccess ||
+      cudaMemsetAsync(c->arena + lay.cme.off, 0, lay.cme.bytes, c->stream) != cudaSuccess ||
+      cudaMemsetAsync(c->arena + lay.bmap.off, 0, lay.bmap.bytes, c->stream) != cudaSuccess ||
+      cudaMemsetAsync(c->arena + lay.U.off, 0, lay.U.bytes, c->stream) != cudaSuccess ||
+      cudaMemsetAsync(c->arena + lay.Us.off, 0, lay.Us.bytes, c->stream) != cudaSuccess)
+    return fail(ICARUS_ERR_CUDA);
+  if ((st = build_geometry(c)) != ICARUS_OK) return fail(st);
+  // shell (ghost) cells of a padded block, in memory order
+  {
+    std::vector<int> sh;
+    const int P0 = desc->block[0] + 2 * NGH, P1 = desc->block[1] + 2 * NGH, P2 = desc->block[2] + 2 * NGH;
+    for (int i = 0; i < P0; i++)
+      for (int j = 0; j < P1; j++)
+        for (int k = 0; k < P2; k++) {
+          const bool in = i >= NGH && i < NGH + desc->block[0] && j >= NGH && j < NGH + desc->block[1] && k >= NGH &&
+                          k < NGH + desc->block[2];
+          if (!in) sh.push_back((i * P1 + j) * P2 + k);
+        }
+    if (cudaMemcpyAsync(c->shell, sh.data(), sizeof(int) * sh.size(), cudaMemcpyHostToDevice, c->stream) !=
+            cudaSuccess ||
+        cudaStreamSynchronize(c->stream) != cudaSuccess)
+      return fail(ICARUS_ERR_CUDA);
+  }
+  // base blocks of every member, Morton order
+  c->mem.assign(nm, Member());
+  const int nb0 = desc->n_cells[0] / desc->block[0], nb1 = desc->n_cells[1] / desc->block[1],
+            nb2 = desc->n_cells[2] / desc->block[2];
+  for (int m = 0; m < nm; m++) {
+    Member &M = c->mem[m];
+    M.max_level = desc->max_level;
+    for (int a = 0; a < nb0; a++)
+      for (int b = 0; b < nb1; b++)
+        for (int e = 0; e < nb2; e++) M.leaves.push_back(Leaf{1, {a, b, e}});
+    std::sort(M.leaves.begin(), M.leaves.end(), [&](const Leaf &x, const Leaf &y) {
+      return morton_key(x, desc->max_level) < morton_key(y, desc->max_level);
+    });
+    build_member_map(c, M);
+  }
+  fill_kp(c);
+  if ((st = upload_tree(c, c->blk)) != ICARUS_OK) return fail(st);
+  default_tiles(c);
+  c->h_tstop.assign(nm, 0.0);
+  // the uniform zero state has no time step: mark dt as unknown (0) until a state is set
+  *out = c;
+  return ICARUS_OK;
+}
+
+void icarus_destroy(icarus_ctx *c) {
+  if (!c) return;
+  if (c->graph) cudaGraphExecDestroy(c->graph);
+  delete c;
+}
+
+icarus_status icarus_set_inner_boundary(icarus_ctx *c, int member, const double *prim) {
+  if (!member_ok(c, member) || !prim) return ICARUS_ERR_ARG;
+  if (c->poisoned) return ICARUS_ERR_STATE;
+  const size_t n = (size_t)NVAR * c->d.n_cells[1] * c->d.n_cells[2];
+  CK(cudaMemcpyAsync(c->bmap + member * n, prim, n * sizeof(double), cudaMemcpyHostToDevice, c->stream));
+  CK(cudaStreamSynchronize(c->stream));
+  c->graph_valid = false;
+  return ICARUS_OK;
+}
+
+icarus_status icarus_inject_cone_cme(icarus_ctx *c, int member, const icarus_cone *p) {
+  if (!member_ok(c, member) || !p) return ICARUS_ERR_ARG;
+  if (c->poisoned) return ICARUS_ERR_STATE;
+  if (!(p->v > 0.0) || !(p->half_width > 0.0) || !(p->half_width < M_PI / 2) || !(p->rho > 0.0) || !(p->p > 0.0))
+    return ICARUS_ERR_ARG;
+  Member &M = c->mem[member];
+  for (const Leaf &l : M.leaves)
+    if (l.level != 1) return ICARUS_ERR_STATE;
+  DevCme dc{};
+  dc.t_start = p->t_start;
+  dc.t_max = p->t_max;
+  dc.colat = p->colat;
+  dc.lon = p->lon;
+  dc.half_width = p->half_width;
+  dc.v = p->v;
+  dc.rho = p->rho;
+  dc.p = p->p;
+  dc.active = 1;
+  dc.pad = 1;  // background speed recorded below
+  M.cme = dc;
+  CK(cudaMemcpyAsync(c->cme + member, &M.cme, sizeof(DevCme), cudaMemcpyHostToDevice, c->stream));
+  const size_t nbc = (size_t)c->d.n_cells[0] * c->d.n_cells[1] * c->d.n_cells[2];
+  vbg_launch(c->kp, c->U, c->prec, member, c->mem_off[member], (int)M.leaves.size(), c->vbg + member * nbc,
+             c->stream);
+  CK(cudaPeekAtLastError());
+  CK(cudaStreamSynchronize(c->stream));
+  return ICARUS_OK;
+}
+
+icarus_status icarus_set_time(icarus_ctx *c, int member, double t) {
+  if (!member_ok(c, member)) return ICARUS_ERR_ARG;
+  CK(cudaMemcpyAsync(c->t + member, &t, sizeof(double), cudaMemcpyHostToDevice, c->stream));
+  CK(cudaStreamSynchronize(c->stream));
+  return ICARUS_OK;
+}
+
+icarus_status icarus_set_member_max_level(icarus_ctx *c, int member, int L) {
+  if (!member_ok(c, member) || L < 1 || L > c->d.max_level) return ICARUS_ERR_ARG;
+  c->mem[member].max_level = L;
+  return ICARUS_OK;
+}
+
+icarus_status icarus_set_tile(icarus_ctx *c, int tj, int tk, int seg) {
+  if (!c) return ICARUS_ERR_ARG;
+  if (tj || tk) {
+    if (!stage_tile_supported(c->prec, tj, tk)) return ICARUS_ERR_ARG;
+    c->tile_j = tj;
+    c->tile_k = tk;
+    default_tiles(c);
+  } else {
+    c->tile_j = c->tile_k = 0;
+    default_tiles(c);
+  }
+  c->seg_len = seg > 0 ? seg : 0;
+  c->graph_valid = false;
+  return ICARUS_OK;
+}
+
+icarus_status icarus_use_graph(icarus_ctx *c, int enable) {
+  if (!c) return ICARUS_ERR_ARG;
+  c->use_graph = enable != 0;
+  return ICARUS_OK;
+}
+
+icarus_status icarus_kernels_per_step(icarus_ctx *c, int *n) {
+  if (!c || !n) return ICARUS_ERR_ARG;
+  int k = 4 + (c->nrlist > 0 ? 1 : 0);  // dt begin, two stages, dt finalize, reflux
+  for (int L = 1; L <= c->max_level_present; L++) {
+    if (!c->lvl_count[L]) continue;
+    k += 2;                              // neighbour ghost pass, both fills
+    for (int d = 0; d < 3; d++)
+      if (c->side_count[L][d]) k += 2;   // physical ghost pass, both fills
+  }
+  *n = k;
+  return ICARUS_OK;
+}
+
+icarus_status icarus_step(icarus_ctx *c, int n_steps, const double *t_stop, double *t_out) {
+  if (!c || n_steps < 0 || !t_stop) return ICARUS_ERR_ARG;
+  if (c->poisoned) return ICARUS_ERR_STATE;
+  const int nm = c->d.n_members;
+  c->h_tstop.assign(t_stop, t_stop + nm);
+  CK(cudaMemcpyAsync(c->tstop, c->h_tstop.data(), sizeof(double) * nm, cudaMemcpyHostToDevice, c->stream));
+  if (n_steps > 0) {
+    if (c->use_graph && c->stream != nullptr) {
+      if (!c->graph_valid) {
+        if (c->graph) {
+          cudaGraphExecDestroy(c->graph);
+          c->graph = nullptr;
+        }
+        cudaGraph_t g = nullptr;
+        CK(cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal));
+        c->kernels_per_step = enqueue_step(c);
+        cudaError_t e = cudaStreamEndCapture(c->stream, &g);
+        if (e != cudaSuccess) {
+          fprintf(stderr, "libicarus: graph capture failed: %s\n", cudaGetErrorString(e));
+          return ICARUS_ERR_CUDA;
+        }
+        e = cudaGraphInstantiate(&c->graph, g, 0);
+        cudaGraphDestroy(g);
+        if (e != cudaSuccess) {
+          fprintf(stderr, "libicarus: graph instantiate failed: %s\n", cudaGetErrorString(e));
+          return ICARUS_ERR_CUDA;
+        }
+        c->graph_valid = true;
+      }
+      for (int s = 0; s < n_steps; s++) CK(cudaGraphLaunch(c->graph, c->stream));
+    } else {
+      for (int s = 0; s < n_steps; s++) c->kernels_per_step = enqueue_step(c);
+      CK(cudaPeekAtLastError());
+    }
+  }
+  // the host copy of t_stop stays alive in the context until the next call
+  if (t_out) {
+    CK(cudaMemcpyAsync(t_out, c->t, sizeof(double) * nm, cudaMemcpyDeviceToHost, c->stream));
+    icarus_status st = check_status(c);
+    if (st != ICARUS_OK) return st;
+  }
+  return ICARUS_OK;
+}
+
+icarus_status icarus_ghost_fill(icarus_ctx *c) {
+  if (!c) return ICARUS_ERR_ARG;
+  if (c->poisoned) return ICARUS_ERR_STATE;
+  enqueue_ghost(c, c->U, 0.0);
+  CK(cudaPeekAtLastError());
+  return ICARUS_OK;
+}
+
+icarus_status icarus_n_leaves(icarus_ctx *c, int member, int *n) {
+  if (!c || !n) return ICARUS_ERR_ARG;
+  if (member < 0) {
+    *n = c->nleaves;
+    return ICARUS_OK;
+  }
+  if (!member_ok(c, member)) return ICARUS_ERR_ARG;
+  *n = (int)c->mem[member].leaves.size();
+  return ICARUS_OK;
+}
+
+icarus_status icarus_get_tree(icarus_ctx *c, int member, int32_t *rows, int capacity, int *n) {
+  if (!member_ok(c, member) || !n) return ICARUS_ERR_ARG;
+  const Member &M = c->mem[member];
+  *n = (int)M.leaves.size();
+  if (!rows) return ICARUS_OK;
+  if (capacity < *n) return ICARUS_ERR_ARG;
+  for (int i = 0; i < *n; i++) {
+    rows[4 * i] = M.leaves[i].level;
+    for (int d = 0; d < 3; d++) rows[4 * i + 1 + d] = M.leaves[i].ix[d];
+  }
+  return ICARUS_OK;
+}
+
+icarus_status icarus_set_state(icarus_ctx *c, int member, const double *host, size_t n, int is_prim) {
+  if (!member_ok(c, member) || !host) return ICARUS_ERR_ARG;
+  if (c->poisoned) return ICARUS_ERR_STATE;
+  const size_t per = (size_t)NVAR * c->kp.icells;
+  const int nl = (int)c->mem[member].leaves.size();
+  if (n != per * nl) return ICARUS_ERR_ARG;
+  const int chunk = (int)(c->lay.staging_doubles / per);
+  for (int s0 = 0; s0 < nl; s0 += chunk) {
+    const int ns = std::min(chunk, nl - s0);
+    CK(cudaMemcpyAsync(c->staging, host + (size_t)s0 * per, sizeof(double) * per * ns, cudaMemcpyHostToDevice,
+                       c->stream));
+    unpack_state_launch(c->kp, c->U, c->prec, c->mem_off[member] + s0, ns, c->staging, is_prim, c->stream);
+    CK(cudaPeekAtLastError());
+    CK(cudaStreamSynchronize(c->stream));
+  }
+  icarus_status st = recompute_dt(c);
+  if (st != ICARUS_OK) return st;
+  CK(cudaStreamSynchronize(c->stream));
+  return ICARUS_OK;
+}
+
+icarus_status icarus_get_state(icarus_ctx *c, int member, double *host, size_t n) {
+  if (!member_ok(c, member) || !host) return ICARUS_ERR_ARG;
+  const size_t per = (size_t)NVAR * c->kp.icells;
+  const int nl = (int)c->mem[member].leaves.size();
+  if (n != per * nl) return ICARUS_ERR_ARG;
+  const int chunk = (int)(c->lay.staging_doubles / per);
+  for (int s0 = 0; s0 < nl; s0 += chunk) {
+    const int ns = std::min(chunk, nl - s0);
+    pack_state_launch(c->kp, c->U, c->prec, c->mem_off[member] + s0, ns, c->staging, c->stream);
+    CK(cudaPeekAtLastError());
+    CK(cudaMemcpyAsync(host + (size_t)s0 * per, c->staging, sizeof(double) * per * ns, cudaMemcpyDeviceToHost,
+                       c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+  }
+  return ICARUS_OK;
+}
+
+icarus_status icarus_get_dt(icarus_ctx *c, double *dt) {
+  if (!c || !dt) return ICARUS_ERR_ARG;
+  CK(cudaMemcpyAsync(dt, c->dt_cfl, sizeof(double) * c->d.n_members, cudaMemcpyDeviceToHost, c->stream));
+  CK(cudaStreamSynchronize(c->stream));
+  return ICARUS_OK;
+}
+
+icarus_status icarus_status_word(icarus_ctx *c, uint32_t *word, uint64_t *floor_hits) {
+  if (!c) return ICARUS_ERR_ARG;
+  unsigned int w = 0;
+  unsigned long long f = 0;
+  CK(cudaMemcpyAsync(&w, c->status, sizeof(w), cudaMemcpyDeviceToHost, c->stream));
+  CK(cudaMemcpyAsync(&f, c->floor_hits, sizeof(f), cudaMemcpyDeviceToHost, c->stream));
+  CK(cudaStreamSynchronize(c->stream));
+  if (word) *word = w;
+  if (floor_hits) *floor_hits = f;
+  return ICARUS_OK;
+}
+
+icarus_status icarus_conservation_sums(icarus_ctx *c, int member, double *out8) {
+  if (!member_ok(c, member) || !out8) return ICARUS_ERR_ARG;
+  const int nl = (int)c->mem[member].leaves.size();
+  sums_launch(c->kp, c->U, c->prec, c->mem_off[member], nl, c->partial, c->stream);
+  CK(cudaPeekAtLastError());
+  std::vector<double> h((size_t)nl * NVAR);
+  CK(cudaMemcpyAsync(h.data(), c->partial, sizeof(double) * h.size(), cudaMemcpyDeviceToHost, c->stream));
+  CK(cudaStreamSynchronize(c->stream));
+  for (int v = 0; v < NVAR; v++) out8[v] = 0.0;
+  for (int b = 0; b < nl; b++)
+    for (int v = 0; v < NVAR; v++) out8[v] += h[(size_t)b * NVAR + v];
+  return ICARUS_OK;
+}
+
+icarus_status icarus_probe(icarus_ctx *c, int member, int n_pts, const double *rtp, double *prim_out) {
+  if (!member_ok(c, member) || n_pts < 0 || n_pts > 4096 || (n_pts && (!rtp || !prim_out))) return ICARUS_ERR_ARG;
+  if (c->poisoned) return ICARUS_ERR_STATE;
+  if (!n_pts) return ICARUS_OK;
+  enqueue_ghost(c, c->U, 0.0);
+  CK(cudaMemcpyAsync(c->probe_in, rtp, sizeof(double) * 3 * n_pts, cudaMemcpyHostToDevice, c->stream));
+  probe_launch2(c->kp, c->U, c->prec, member, c->d.max_level, n_pts, c->probe_in, c->probe_out, c->stream);
+  CK(cudaPeekAtLastError());
+  CK(cudaMemcpyAsync(prim_out, c->probe_out, sizeof(double) * NVAR * n_pts, cudaMemcpyDeviceToHost, c->stream));
+  return check_status(c);
+}
+
+icarus_status icarus_flag_refine(icarus_ctx *c, const icarus_refine *crit, int8_t *flags_out) {
+  if (!c || !crit) return ICARUS_ERR_ARG;
+  if (c->poisoned) return ICARUS_ERR_STATE;
+  enqueue_ghost(c, c->U, 0.0);
+  estimator_launch(c->kp, c->U, c->prec, 0, c->nleaves, crit->e_refine, crit->e_coarsen, crit->eps, crit->dv,
+                   c->flags, c->stream);
+  CK(cudaPeekAtLastError());
+  c->hflags.assign(c->nleaves, 0);
+  CK(cudaMemcpyAsync(c->hflags.data(), c->flags, c->nleaves, cudaMemcpyDeviceToHost, c->stream));
+  CK(cudaStreamSynchronize(c->stream));
+  if (flags_out) memcpy(flags_out, c->hflags.data(), c->nleaves);
+  c->flags_valid = true;
+  return ICARUS_OK;
+}
+
+icarus_status icarus_set_flags(icarus_ctx *c, const int8_t *flags) {
+  if (!c || !flags) return ICARUS_ERR_ARG;
+  c->hflags.assign((const signed char *)flags, (const signed char *)flags + c->nleaves);
+  c->flags_valid = true;
+  return ICARUS_OK;
+}
+
+icarus_status icarus_regrid(icarus_ctx *c) {
+  if (!c) return ICARUS_ERR_ARG;
+  if (c->poisoned) return ICARUS_ERR_STATE;
+  if (!c->flags_valid) return ICARUS_ERR_STATE;
+  if (c->d.max_level == 1) {
+    c->flags_valid = false;
+    return ICARUS_OK;
+  }
+  // fill ghosts of the current state: prolongation reads the parents' halos
+  enqueue_ghost(c, c->U, 0.0);
+  CK(cudaPeekAtLastError());
+  std::vector<MoveOp> ops;
+  std::vector<Member> next(c->d.n_members);
+  int slot = 0;
+  for (int m = 0; m < c->d.n_members; m++) {
+    const Member &M = c->mem[m];
+    const int n = (int)M.leaves.size();
+    const signed char *fl = c->hflags.data() + c->mem_off[m];
+    std::vector<int> T(n);
+    for (int i = 0; i < n; i++) {
+      T[i] = M.leaves[i].level;
+      if (fl[i] > 0 && M.leaves[i].level < M.max_level) T[i]++;
+    }
+    // complete sibling families flagged -1 coarsen (a family is contiguous in
+    // Morton order and starts at child 0)
+    for (int i = 0; i + 7 < n; i++) {
+      const Leaf &l = M.leaves[i];
+      if (l.level == 1 || (l.ix[0] & 1) || (l.ix[1] & 1) || (l.ix[2] & 1)) continue;
+      bool fam = true;
+      for (int q = 0; q < 8 && fam; q++) {
+        const Leaf &s = M.leaves[i + q];
+        const int o[3] = {(q >> 2) & 1, (q >> 1) & 1, q & 1};
+        if (s.level != l.level || fl[i + q] >= 0) fam = false;
+        for (int d = 0; d < 3; d++)
+          if (s.ix[d] != l.ix[d] + o[d]) fam = false;
+      }
+      if (fam)
+        for (int q = 0; q < 8; q++) T[i + q] = l.level - 1;
+    }
+    // 2:1 balance, least fixed point
+    std::vector<std::vector<int>> nb(n);
+    for (int i = 0; i < n; i++) neighbours(c, M, i, nb[i]);
+    bool changed = true;
+    while (changed) {
+      changed = false;
+      for (int i = 0; i < n; i++) {
+        for (int j : nb[i]) {
+          if (T[j] > T[i] + 1) {
+            if (T[i] < M.leaves[i].level) {
+              // cancel the family's coarsening: find child 0 of the family
+              const Leaf &l = M.leaves[i];
+              int b[3] = {l.ix[0] & ~1, l.ix[1] & ~1, l.ix[2] & ~1};
+              const int first = M.map[l.level][map_index(c, l.level, b)];
+              for (int q = 0; q < 8; q++) T[first + q] = l.level;
+            } else {
+              T[i] = M.leaves[i].level + 1;
+            }
+            changed = true;
+          }
+        }
+      }
+    }
+    // new leaf list (Morton order preserved) and data movement
+    Member &N = next[m];
+    N.max_level = M.max_level;
+    N.cme = M.cme;
+    for (int i = 0; i < n;) {
+      const Leaf &l = M.leaves[i];
+      const int old_slot = c->mem_off[m] + i;
+      if (T[i] == l.level + 1) {
+        for (int ch = 0; ch < 8; ch++) {
+          Leaf k{l.level + 1, {2 * l.ix[0] + ((ch >> 2) & 1), 2 * l.ix[1] + ((ch >> 1) & 1), 2 * l.ix[2] + (ch & 1)}};
+          N.leaves.push_back(k);
+          MoveOp op{};
+          op.kind = 1;
+          op.dst = slot++;
+          op.src[0] = old_slot;
+          ops.push_back(op);
+        }
+        i++;
+      } else if (T[i] == l.level - 1) {
+        Leaf p{l.level - 1, {l.ix[0] >> 1, l.ix[1] >> 1, l.ix[2] >> 1}};
+        N.leaves.push_back(p);
+        MoveOp op{};
+        op.kind = 2;
+        op.dst = slot++;
+        for (int q = 0; q < 8; q++) op.src[q] = old_slot + q;
+        ops.push_back(op);
+        i += 8;
+      } else {
+        N.leaves.push_back(l);
+        MoveOp op{};
+        op.kind = 0;
+        op.dst = slot++;
+        op.src[0] = old_slot;
+        ops.push_back(op);
+        i++;
+      }
+    }
+  }
+  if (slot > c->lay.max_blocks) return ICARUS_ERR_CAPACITY;
+  // old tables stay valid for the movement kernel: build the new ones in the
+  // alternate block table
+  KParams kp_old = c->kp;
+  std::vector<Member> old = std::move(c->mem);
+  c->mem = std::move(next);
+  for (Member &M : c->mem) build_member_map(c, M);
+  // the level maps are only read through the new tables after the move
+  std::vector<DevBlock> old_hblk = c->hblk;
+  const int old_nleaves = c->nleaves;
+  (void)old_nleaves;
+  // upload the new block table into blk_alt first (the move kernel needs the
+  // new block coordinates and the old table at the same time)
+  icarus_status st;
+  {
+    // compute the new host block table without touching device level maps yet
+    std::vector<DevBlock> nb;
+    int s2 = 0;
+    for (int m = 0; m < c->d.n_members; m++)
+      for (const Leaf &l : c->mem[m].leaves) {
+        DevBlock B{};
+        B.member = m;
+        B.level = l.level;
+        for (int d = 0; d < 3; d++) B.ix[d] = l.ix[d];
+        nb.push_back(B);
+        s2++;
+      }
+    CK(cudaMemcpyAsync(c->blk_alt, nb.data(), sizeof(DevBlock) * nb.size(), cudaMemcpyHostToDevice, c->stream));
+    CK(cudaMemcpyAsync(c->ops, ops.data(), sizeof(MoveOp) * ops.size(), cudaMemcpyHostToDevice, c->stream));
+    regrid_move_launch2(kp_old, c->U, c->Ualt, c->blk_alt, c->prec, c->ops, (int)ops.size(), c->stream);
+    CK(cudaPeekAtLastError());
+    CK(cudaStreamSynchronize(c->stream));
+  }
+  std::swap(c->U, c->Ualt);
+  if ((st = upload_tree(c, c->blk)) != ICARUS_OK) return st;
+  fill_kp(c);
+  st = recompute_dt(c);
+  if (st != ICARUS_OK) return st;
+  CK(cudaStreamSynchronize(c->stream));
+  c->flags_valid = false;
+  return ICARUS_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,457 @@
+// Ghost-cell fill, reflux and time-step kernels.
+//
+// Two ghost layers per block (arXiv 2211.12867, Sect. 2.1).  Ghosts are
+// filled level by level, coarse to fine, so that a prolongation always reads
+// a coarse block whose own ghosts are complete:
+//   * same-level leaf      -> copy of its interior cell
+//   * coarser leaf          -> conservative prolongation: parent value plus
+//                             monotonised-central slopes of the conserved
+//                             variables times the offset of the child's
+//                             volume-weighted centre (falls back to the parent
+//                             value when a child's pressure or density would
+//                             not be positive)
+//   * finer leaves          -> volume-weighted restriction of the 8 children
+//   * outside the domain    -> physical boundary: fixed inner boundary map
+//                             with the cone CME overlay (Eqs. 1-4),
+//                             zero-gradient copy, or reflection; applied per
+//                             direction r, theta, phi in that order over the
+//                             whole padded slab.
+// Reflux: a coarse leaf face next to finer leaves takes the sum of the fine
+// area-weighted fluxes of the corrector stage (exact conservation across
+// levels on the stretched spherical grid).
+#include "mhd_device.cuh"
+
+namespace {
+
+__device__ __forceinline__ int wrap_dim(const KParams &kp, int L, int d, int G, bool &inside) {
+  const int N = kp.n_base_cells[d] << (L - 1);
+  if (kp.bc_lo[d] == 0) {  // periodic
+    inside = true;
+    G %= N;
+    return G < 0 ? G + N : G;
+  }
+  inside = G >= 0 && G < N;
+  return G;
+}
+
+// slot of the level-L leaf holding cell G (>=0), -1 coarser, -2 refined
+__device__ __forceinline__ int lookup(const KParams &kp, int member, int L, const int *G) {
+  const long long off = kp.lmap_off[member * (MAXLEV + 1) + L];
+  const int s = L - 1;
+  const int b0 = G[0] / kp.nb[0], b1 = G[1] / kp.nb[1], b2 = G[2] / kp.nb[2];
+  const int n1 = kp.nbase[1] << s, n2 = kp.nbase[2] << s;
+  return kp.lmap[off + ((long long)b0 * n1 + b1) * n2 + b2];
+}
+
+template <typename real>
+__device__ __forceinline__ size_t cell_index(const KParams &kp, int slot, int v, int p0, int p1, int p2) {
+  return ((((size_t)slot * NVAR + v) * kp.P[0] + p0) * kp.P[1] + p1) * kp.P[2] + p2;
+}
+
+// prolonged value of child `ch` of coarse cell Ic (global at level Lc) held
+// by leaf slot cs; positivity is checked on all 8 children.
+template <typename real>
+__device__ void prolong_value(const KParams &kp, const real *U, int cs, int Lc, const int *Ic, int ch, real *out) {
+  const DevBlock C = kp.blk[cs];
+  int pc[3];
+#pragma unroll
+  for (int d = 0; d < 3; d++) pc[d] = Ic[d] - C.ix[d] * kp.nb[d] + NGH;
+  real up[NVAR], s[3][NVAR];
+#pragma unroll
+  for (int v = 0; v < NVAR; v++) {
+    up[v] = U[cell_index<real>(kp, cs, v, pc[0], pc[1], pc[2])];
+    s[0][v] = mc_slope<real>(U[cell_index<real>(kp, cs, v, pc[0] - 1, pc[1], pc[2])], up[v],
+                             U[cell_index<real>(kp, cs, v, pc[0] + 1, pc[1], pc[2])]);
+    s[1][v] = mc_slope<real>(U[cell_index<real>(kp, cs, v, pc[0], pc[1] - 1, pc[2])], up[v],
+                             U[cell_index<real>(kp, cs, v, pc[0], pc[1] + 1, pc[2])]);
+    s[2][v] = mc_slope<real>(U[cell_index<real>(kp, cs, v, pc[0], pc[1], pc[2] - 1)], up[v],
+                             U[cell_index<real>(kp, cs, v, pc[0], pc[1], pc[2] + 1)]);
+  }
+  const real *d0 = GeoSel<real>::dlt(kp.geo, Lc, 0), *d1 = GeoSel<real>::dlt(kp.geo, Lc, 1),
+             *d2 = GeoSel<real>::dlt(kp.geo, Lc, 2);
+  const real gamma = (real)kp.gamma;
+  bool ok = true;
+  for (int c = 0; c < 8; c++) {
+    const real a = d0[2 * Ic[0] + ((c >> 2) & 1)], b = d1[2 * Ic[1] + ((c >> 1) & 1)], e = d2[2 * Ic[2] + (c & 1)];
+    real u[NVAR];
+#pragma unroll
+    for (int v = 0; v < NVAR; v++) u[v] = ((up[v] + s[0][v] * a) + s[1][v] * b) + s[2][v] * e;
+    if (!(u[0] > real(0)) || !(pressure_of<real>(u, gamma) > real(0))) ok = false;
+    if (c == ch) {
+#pragma unroll
+      for (int v = 0; v < NVAR; v++) out[v] = u[v];
+    }
+  }
+  if (!ok) {
+#pragma unroll
+    for (int v = 0; v < NVAR; v++) out[v] = up[v];
+  }
+}
+
+// volume-weighted mean of the 8 level-(L+1) cells under cell G of level L
+template <typename real>
+__device__ bool restrict_value(const KParams &kp, const real *U, int member, int L, const int *G, real *out) {
+  const LevelGeo<real> &F = GeoSel<real>::get(kp.geo, L + 1);
+  real sum[NVAR];
+#pragma unroll
+  for (int v = 0; v < NVAR; v++) sum[v] = real(0);
+  real vs = real(0);
+  for (int c = 0; c < 8; c++) {
+    int f[3] = {2 * G[0] + ((c >> 2) & 1), 2 * G[1] + ((c >> 1) & 1), 2 * G[2] + (c & 1)};
+    const int fs = lookup(kp, member, L + 1, f);
+    if (fs < 0) return false;
+    const DevBlock FB = kp.blk[fs];
+    const real V = F.dr3[f[0] + NGH] * F.dcos[f[1] + NGH] * F.dphi;
+    const int q0 = f[0] - FB.ix[0] * kp.nb[0] + NGH, q1 = f[1] - FB.ix[1] * kp.nb[1] + NGH,
+              q2 = f[2] - FB.ix[2] * kp.nb[2] + NGH;
+#pragma unroll
+    for (int v = 0; v < NVAR; v++) sum[v] += V * U[cell_index<real>(kp, fs, v, q0, q1, q2)];
+    vs += V;
+  }
+#pragma unroll
+  for (int v = 0; v < NVAR; v++) out[v] = sum[v] / vs;
+  return true;
+}
+
+template <typename real>
+__global__ void k_ghost_neighbour(const KParams kp, real *U, const int *list, const int *shell, int nshell,
+                                  int L) {
+  const int s = blockIdx.y * blockDim.x + threadIdx.x;
+  if (s >= nshell) return;
+  const int slot = list[blockIdx.x];
+  const DevBlock B = kp.blk[slot];
+  const int lin = shell[s];
+  const int p2 = lin % kp.P[2], p1 = (lin / kp.P[2]) % kp.P[1], p0 = lin / (kp.P[2] * kp.P[1]);
+  const int p[3] = {p0, p1, p2};
+  int G[3];
+#pragma unroll
+  for (int d = 0; d < 3; d++) {
+    bool in;
+    G[d] = wrap_dim(kp, L, d, B.ix[d] * kp.nb[d] + p[d] - NGH, in);
+    if (!in) return;  // physical boundary pass fills it
+  }
+  real val[NVAR];
+  const int o = lookup(kp, B.member, L, G);
+  if (o >= 0) {
+    const DevBlock O = kp.blk[o];
+#pragma unroll
+    for (int v = 0; v < NVAR; v++)
+      val[v] = U[cell_index<real>(kp, o, v, G[0] - O.ix[0] * kp.nb[0] + NGH, G[1] - O.ix[1] * kp.nb[1] + NGH,
+                                  G[2] - O.ix[2] * kp.nb[2] + NGH)];
+  } else if (o == -1) {
+    int Ic[3] = {G[0] >> 1, G[1] >> 1, G[2] >> 1};
+    const int cs = lookup(kp, B.member, L - 1, Ic);
+    if (cs < 0) {
+      atomicOr(kp.status, ST_NAN);
+      return;
+    }
+    prolong_value<real>(kp, U, cs, L - 1, Ic, ((G[0] & 1) << 2) | ((G[1] & 1) << 1) | (G[2] & 1), val);
+  } else {
+    if (!restrict_value<real>(kp, U, B.member, L, G, val)) {
+      atomicOr(kp.status, ST_NAN);
+      return;
+    }
+  }
+#pragma unroll
+  for (int v = 0; v < NVAR; v++) U[cell_index<real>(kp, slot, v, p0, p1, p2)] = val[v];
+}
+
+// inner boundary state (FP64): map of the containing base cell, cone CME overlay
+__device__ void inner_state(const KParams &kp, int member, int L, int J, int K, double t, double *u) {
+  const int n1 = kp.n_base_cells[1], n2 = kp.n_base_cells[2];
+  const int jb = J >> (L - 1), kb = K >> (L - 1);
+  const double *m = kp.bmap + (size_t)member * NVAR * n1 * n2;
+  double w[NVAR];
+#pragma unroll
+  for (int v = 0; v < NVAR; v++) w[v] = m[((size_t)v * n1 + jb) * n2 + kb];
+  const DevCme c = kp.cme[member];
+  if (c.active) {
+    const LevelGeo<double> &G = kp.geo->d[L];
+    const double th = G.tc[J + NGH], ph = G.pc[K + NGH];
+    const double R = G.rf[NGH];
+    const double tau = t - c.t_start;
+    if (tau >= 0.0 && tau <= c.t_max) {
+      const double rh = R * sin(c.half_width);
+      const double Rc = tau * c.v + R - rh;
+      const double arg = (Rc * Rc + R * R - rh * rh) / (2.0 * Rc * R);
+      if (!(arg > 1.0)) {
+        const double open = acos(arg);
+        double a = sin(th) * sin(c.colat) * cos(ph - c.lon) + cos(th) * cos(c.colat);
+        a = a > 1.0 ? 1.0 : (a < -1.0 ? -1.0 : a);
+        if (acos(a) <= open) {
+          w[0] = c.rho;
+          w[1] = c.v;
+          w[2] = 0.0;
+          w[3] = -kp.omega * R * sin(th);
+          w[4] = c.p;
+          w[5] = w[6] = w[7] = 0.0;
+        }
+      }
+    }
+  }
+  prim2cons<double>(w, u, kp.gamma);
+}
+
+// physical boundary of direction `dir`; sides[n] = (slot, side)
+template <typename real>
+__global__ void k_ghost_physical(const KParams kp, real *U, const int2 *sides, int dir, int L, double tfac) {
+  const int2 sd = sides[blockIdx.x];
+  const int slot = sd.x, side = sd.y;
+  const int da = dir == 0 ? 1 : 0, db = dir == 2 ? 1 : 2;
+  const int Pa = kp.P[da], Pb = kp.P[db];
+  const int idx = blockIdx.y * blockDim.x + threadIdx.x;
+  if (idx >= NGH * Pa * Pb) return;
+  const int gl = idx / (Pa * Pb), r = idx % (Pa * Pb), a = r / Pb, b = r % Pb;
+  const int bc = side ? kp.bc_hi[dir] : kp.bc_lo[dir];
+  const int nbd = kp.nb[dir];
+  const int pg = side ? NGH + nbd + gl : NGH - 1 - gl;
+  const int pn = side ? NGH + nbd - 1 : NGH;
+  const int pm = side ? NGH + nbd - 1 - gl : NGH + gl;
+  int q[3], s[3];
+  q[dir] = pg;
+  q[da] = a;
+  q[db] = b;
+  s[da] = a;
+  s[db] = b;
+  const DevBlock B = kp.blk[slot];
+  if (bc == 3) {  // inner boundary (r low)
+    bool in1, in2;
+    const int J = wrap_dim(kp, L, 1, B.ix[1] * kp.nb[1] + q[1] - NGH, in1);
+    const int K = wrap_dim(kp, L, 2, B.ix[2] * kp.nb[2] + q[2] - NGH, in2);
+    if (!in1 || !in2) return;
+    const double t = kp.t[B.member] + tfac * kp.dt_used[B.member];
+    double u[NVAR];
+    inner_state(kp, B.member, L, J, K, t, u);
+#pragma unroll
+    for (int v = 0; v < NVAR; v++) U[cell_index<real>(kp, slot, v, q[0], q[1], q[2])] = (real)u[v];
+    return;
+  }
+  s[dir] = bc == 2 ? pm : pn;
+#pragma unroll
+  for (int v = 0; v < NVAR; v++) {
+    real x = U[cell_index<real>(kp, slot, v, s[0], s[1], s[2])];
+    if (bc == 2 && (v == 1 + dir || v == 5 + dir)) x = -x;
+    U[cell_index<real>(kp, slot, v, q[0], q[1], q[2])] = x;
+  }
+}
+
+// reflux of coarse blocks with finer face neighbours; one CTA per block
+template <typename real>
+__global__ void k_reflux(const KParams kp, real *U, const real *flux, const int *list) {
+  const int slot = list[blockIdx.x];
+  const DevBlock B = kp.blk[slot];
+  const double dtm = kp.dt_used[B.member];
+  if (!(dtm > 0.0)) return;
+  const real dt = (real)dtm;
+  const int L = B.level;
+  const int nb0 = kp.nb[0], nb1 = kp.nb[1], nb2 = kp.nb[2];
+  const int fc[3] = {nb1 * nb2, nb0 * nb2, nb0 * nb1};
+  const size_t fstride = (size_t)NVAR * 2 * (fc[0] + fc[1] + fc[2]);
+  size_t foff[6];
+  {
+    size_t o = 0;
+    for (int f = 0; f < 6; f++) {
+      foff[f] = o;
+      o += (size_t)NVAR * fc[f / 2];
+    }
+  }
+  const LevelGeo<real> &G = GeoSel<real>::get(kp.geo, L);
+  for (int f = 0; f < 6; f++) {
+    if (B.nbr[f] != NB_FINER) continue;
+    const int d = f / 2, hi = f % 2;
+    const int d1 = d == 0 ? 1 : 0, d2 = d == 2 ? 1 : 2;
+    for (int t = threadIdx.x; t < fc[d]; t += blockDim.x) {
+      const int t1 = t / kp.nb[d2], t2 = t % kp.nb[d2];
+      int Gc[3];
+      Gc[d1] = B.ix[d1] * kp.nb[d1] + t1;
+      Gc[d2] = B.ix[d2] * kp.nb[d2] + t2;
+      Gc[d] = hi ? (B.ix[d] + 1) * kp.nb[d] : B.ix[d] * kp.nb[d] - 1;  // coarse cell across
+      real fs[NVAR];
+#pragma unroll
+      for (int v = 0; v < NVAR; v++) fs[v] = real(0);
+      for (int a = 0; a < 2; a++)
+        for (int c = 0; c < 2; c++) {
+          int F[3];
+          F[d] = hi ? 2 * Gc[d] : 2 * Gc[d] + 1;
+          F[d1] = 2 * Gc[d1] + a;
+          F[d2] = 2 * Gc[d2] + c;
+          bool in;
+          for (int e = 0; e < 3; e++) F[e] = wrap_dim(kp, L + 1, e, F[e], in);
+          const int fsl = lookup(kp, B.member, L + 1, F);
+          if (fsl < 0) {
+            atomicOr(kp.status, ST_NAN);
+            continue;
+          }
+          const DevBlock FB = kp.blk[fsl];
+          const int s1 = F[d1] - FB.ix[d1] * kp.nb[d1], s2 = F[d2] - FB.ix[d2] * kp.nb[d2];
+          const real *src = flux + (size_t)fsl * fstride + foff[2 * d + (hi ? 0 : 1)];
+#pragma unroll
+          for (int v = 0; v < NVAR; v++) fs[v] += src[(size_t)v * fc[d] + s1 * kp.nb[d2] + s2];
+        }
+      int q[3];
+      q[d] = hi ? NGH + kp.nb[d] - 1 : NGH;
+      q[d1] = NGH + t1;
+      q[d2] = NGH + t2;
+      const int I = B.ix[0] * nb0 + q[0] - NGH, J = B.ix[1] * nb1 + q[1] - NGH;
+      const real V = G.dr3[I + NGH] * G.dcos[J + NGH] * G.dphi;
+      const real *own = flux + (size_t)slot * fstride + foff[f];
+      const real sg = hi ? real(-1) : real(1);
+#pragma unroll
+      for (int v = 0; v < NVAR; v++) {
+        const size_t ci = cell_index<real>(kp, slot, v, q[0], q[1], q[2]);
+        U[ci] += sg * dt / V * (fs[v] - own[(size_t)v * fc[d] + t]);
+      }
+    }
+    __syncthreads();
+  }
+  // floors and CFL contribution of every corrected cell
+  const real gamma = (real)kp.gamma, pfl = (real)kp.p_floor, rfl = (real)kp.rho_floor;
+  double acc = 0.0;
+  long long hits = 0;
+  for (int f = 0; f < 6; f++) {
+    if (B.nbr[f] != NB_FINER) continue;
+    const int d = f / 2, hi = f % 2;
+    const int d1 = d == 0 ? 1 : 0, d2 = d == 2 ? 1 : 2;
+    for (int t = threadIdx.x; t < fc[d]; t += blockDim.x) {
+      const int t1 = t / kp.nb[d2], t2 = t % kp.nb[d2];
+      int q[3];
+      q[d] = hi ? NGH + kp.nb[d] - 1 : NGH;
+      q[d1] = NGH + t1;
+      q[d2] = NGH + t2;
+      real u[NVAR];
+#pragma unroll
+      for (int v = 0; v < NVAR; v++) u[v] = U[cell_index<real>(kp, slot, v, q[0], q[1], q[2])];
+      hits += apply_floors<real>(u, gamma, pfl, rfl);
+#pragma unroll
+      for (int v = 0; v < NVAR; v++) U[cell_index<real>(kp, slot, v, q[0], q[1], q[2])] = u[v];
+      real w[NVAR];
+      cons2prim<real>(u, w, gamma, pfl);
+      const int I = B.ix[0] * nb0 + q[0] - NGH + NGH, J = B.ix[1] * nb1 + q[1] - NGH + NGH;
+      real dx0 = G.dr[I], dx1 = G.dth[J], dx2 = G.dphi;
+      if (kp.geometry == 0) {
+        dx1 *= G.rc[I];
+        dx2 *= G.rc[I] * G.sintc[J];
+      }
+      const real sp = (RT<real>::abs_(w[1]) + fast_speed<real, 0>(w, gamma)) / dx0 +
+                      (RT<real>::abs_(w[2]) + fast_speed<real, 1>(w, gamma)) / dx1 +
+                      (RT<real>::abs_(w[3]) + fast_speed<real, 2>(w, gamma)) / dx2;
+      acc = fmax(acc, (double)sp);
+    }
+    __syncthreads();
+  }
+  for (int o = 16; o > 0; o >>= 1) {
+    acc = fmax(acc, __shfl_xor_sync(0xffffffffu, acc, o));
+    hits += __shfl_xor_sync(0xffffffffu, hits, o);
+  }
+  if ((threadIdx.x & 31) == 0) {
+    if (acc > 0.0) atomic_max_pos(&kp.inv_max[B.member], acc);
+    if (hits) atomicAdd(kp.floor_hits, (unsigned long long)hits);
+  }
+}
+
+__global__ void k_dt_begin(const KParams kp, const double *tstop) {
+  const int m = blockIdx.x * blockDim.x + threadIdx.x;
+  if (m >= kp.n_members) return;
+  double dt = fmin(kp.dt_cfl[m], tstop[m] - kp.t[m]);
+  kp.dt_used[m] = dt > 0.0 ? dt : 0.0;
+}
+
+__global__ void k_dt_finalize(const KParams kp, double cfl) {
+  const int m = blockIdx.x * blockDim.x + threadIdx.x;
+  if (m >= kp.n_members) return;
+  const double dt = kp.dt_used[m];
+  if (dt > 0.0) {
+    kp.t[m] += dt;
+    const double inv = __longlong_as_double((long long)kp.inv_max[m]);
+    if (inv > 0.0) kp.dt_cfl[m] = cfl / inv;
+  }
+  kp.inv_max[m] = 0ull;
+}
+
+// CFL time step of the whole current state (after set_state / regrid / init)
+template <typename real>
+__global__ void k_dt_full(const KParams kp, const real *U) {
+  const int slot = blockIdx.x;
+  const DevBlock B = kp.blk[slot];
+  const LevelGeo<real> &G = GeoSel<real>::get(kp.geo, B.level);
+  const real gamma = (real)kp.gamma, pfl = (real)kp.p_floor;
+  double acc = 0.0;
+  for (int c = threadIdx.x; c < kp.icells; c += blockDim.x) {
+    const int k = c % kp.nb[2], j = (c / kp.nb[2]) % kp.nb[1], i = c / (kp.nb[2] * kp.nb[1]);
+    real u[NVAR], w[NVAR];
+#pragma unroll
+    for (int v = 0; v < NVAR; v++) u[v] = U[cell_index<real>(kp, slot, v, i + NGH, j + NGH, k + NGH)];
+    cons2prim<real>(u, w, gamma, pfl);
+    const int I = B.ix[0] * kp.nb[0] + i + NGH, J = B.ix[1] * kp.nb[1] + j + NGH;
+    real dx0 = G.dr[I], dx1 = G.dth[J], dx2 = G.dphi;
+    if (kp.geometry == 0) {
+      dx1 *= G.rc[I];
+      dx2 *= G.rc[I] * G.sintc[J];
+    }
+    const real sp = (RT<real>::abs_(w[1]) + fast_speed<real, 0>(w, gamma)) / dx0 +
+                    (RT<real>::abs_(w[2]) + fast_speed<real, 1>(w, gamma)) / dx1 +
+                    (RT<real>::abs_(w[3]) + fast_speed<real, 2>(w, gamma)) / dx2;
+    acc = fmax(acc, (double)sp);
+  }
+  for (int o = 16; o > 0; o >>= 1) acc = fmax(acc, __shfl_xor_sync(0xffffffffu, acc, o));
+  if ((threadIdx.x & 31) == 0 && acc > 0.0) atomic_max_pos(&kp.inv_max[B.member], acc);
+}
+
+__global__ void k_dt_from_max(const KParams kp, double cfl) {
+  const int m = blockIdx.x * blockDim.x + threadIdx.x;
+  if (m >= kp.n_members) return;
+  const double inv = __longlong_as_double((long long)kp.inv_max[m]);
+  kp.dt_cfl[m] = inv > 0.0 ? cfl / inv : 0.0;
+  kp.inv_max[m] = 0ull;
+}
+
+}  // namespace
+
+void ghost_neighbour_launch(const KParams &kp, void *U, int precision, const int *list, int nlist, const int *shell,
+                            int nshell, int level, cudaStream_t s) {
+  if (nlist <= 0) return;
+  dim3 grid(nlist, (nshell + 255) / 256);
+  if (precision)
+    k_ghost_neighbour<float><<<grid, 256, 0, s>>>(kp, (float *)U, list, shell, nshell, level);
+  else
+    k_ghost_neighbour<double><<<grid, 256, 0, s>>>(kp, (double *)U, list, shell, nshell, level);
+}
+
+void ghost_physical_launch(const KParams &kp, void *U, int precision, const int2 *sides, int nsides, int dir,
+                           int level, double tfac, cudaStream_t s) {
+  if (nsides <= 0) return;
+  const int da = dir == 0 ? 1 : 0, db = dir == 2 ? 1 : 2;
+  const int n = NGH * kp.P[da] * kp.P[db];
+  dim3 grid(nsides, (n + 127) / 128);
+  if (precision)
+    k_ghost_physical<float><<<grid, 128, 0, s>>>(kp, (float *)U, sides, dir, level, tfac);
+  else
+    k_ghost_physical<double><<<grid, 128, 0, s>>>(kp, (double *)U, sides, dir, level, tfac);
+}
+
+void reflux_launch(const KParams &kp, void *U, const void *flux, int precision, const int *list, int nlist,
+                   cudaStream_t s) {
+  if (nlist <= 0) return;
+  if (precision)
+    k_reflux<float><<<nlist, 256, 0, s>>>(kp, (float *)U, (const float *)flux, list);
+  else
+    k_reflux<double><<<nlist, 256, 0, s>>>(kp, (double *)U, (const double *)flux, list);
+}
+
+void dt_begin_launch(const KParams &kp, const double *tstop, cudaStream_t s) {
+  k_dt_begin<<<(kp.n_members + 127) / 128, 128, 0, s>>>(kp, tstop);
+}
+
+void dt_finalize_launch(const KParams &kp, double cfl, cudaStream_t s) {
+  k_dt_finalize<<<(kp.n_members + 127) / 128, 128, 0, s>>>(kp, cfl);
+}
+
+void dt_full_launch(const KParams &kp, const void *U, int precision, int nleaves, double cfl, cudaStream_t s) {
+  if (nleaves > 0) {
+    if (precision)
+      k_dt_full<float><<<nleaves, 256, 0, s>>>(kp, (const float *)U);
+    else
+      k_dt_full<double><<<nleaves, 256, 0, s>>>(kp, (const double *)U);
+  }
+  k_dt_from_max<<<(kp.n_members + 127) / 128, 128, 0, s>>>(kp, cfl);
+}

@@ -1,0 +1,411 @@
+// Stage operator of the midpoint predictor-corrector on every leaf block.
+//
+//   predictor  U*      = U^n + dt/2 L(U^n)
+//   corrector  U^{n+1} = U^n + dt   L(U*) + cleaning(U*)
+//
+// L(U) = -(1/V) sum_faces A F_TVDLF + S_geometric + S_rotation (arXiv
+// 2211.12867, Sect. 2.1: TVDLF with the Woodward limiter, second order in space
+// and time, ideal MHD in the co-rotating frame, parabolic div B cleaning).
+// Geometric sources come from the spherical divergence of the momentum and
+// induction tensors with the pressure parts in face-area-difference form (a
+// uniform state is preserved to round-off); rotation sources are the Coriolis
+// and centrifugal forces with the centrifugal work.  Cleaning is the
+// diffusive (parabolic) form dB = C_d h^2 grad(div B*), de = B*.dB, with
+// central differences and h^-2 = sum_d dx_d^-2.
+//
+// GPU design: one CTA owns a (theta x phi) tile of one block and marches along
+// r.  Primitives of five consecutive r-planes live in a shared-memory ring
+// (each cell of the tile plus its 2-cell halo is loaded and converted once per
+// CTA); the r-face flux is carried in registers from one plane to the next;
+// theta and phi face fluxes are computed once per face into shared memory and
+// read by the two cells that share the face; div B of the corrector lives in a
+// 4-plane ring.  The corrector also accumulates the CFL time step of the new
+// state (FP64 max of the inverse time step per member) and stores the
+// area-weighted face fluxes of block faces that border a different level for
+// the reflux.  The grid is persistent: CTAs stride over (block, tile,
+// r-segment) work items of all levels and all ensemble members.
+#include <cstdio>
+
+#include "mhd_device.cuh"
+
+namespace {
+
+template <typename real>
+struct StageSmem {
+  static constexpr size_t bytes(int tj, int tk) {
+    return sizeof(real) * (size_t)(5 * NVAR * (tj + 4) * (tk + 4) + NVAR * (tj + 1) * tk +
+                                   NVAR * tj * (tk + 1) + 4 * (tj + 2) * (tk + 2));
+  }
+};
+
+__device__ __forceinline__ void flush_acc(const KParams &kp, double &acc, int member, long long &hits) {
+  // warp max of the inverse time step, one atomic per warp
+  for (int o = 16; o > 0; o >>= 1) acc = fmax(acc, __shfl_xor_sync(0xffffffffu, acc, o));
+  long long h = hits;
+  for (int o = 16; o > 0; o >>= 1) h += __shfl_xor_sync(0xffffffffu, h, o);
+  if ((threadIdx.x & 31) == 0 && member >= 0) {
+    if (acc > 0.0) atomic_max_pos(&kp.inv_max[member], acc);
+    if (h) atomicAdd(kp.floor_hits, (unsigned long long)h);
+  }
+  acc = 0.0;
+  hits = 0;
+}
+
+template <typename real, int TJ, int TK, bool S2>
+__global__ void __launch_bounds__(TJ *TK, (sizeof(real) == 4 ? 2 : 1))
+    k_stage(const KParams kp, const StageLaunch sl) {
+  constexpr int NT = TJ * TK, RJ = TJ + 4, RK = TK + 4, RP = RJ * RK;
+  constexpr int DJ = TJ + 2, DK = TK + 2, DP = DJ * DK;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  real *ring = reinterpret_cast<real *>(smem_raw);
+  real *fth = ring + 5 * NVAR * RP;
+  real *fph = fth + NVAR * (TJ + 1) * TK;
+  real *dring = fph + NVAR * TJ * (TK + 1);
+
+  const int tid = threadIdx.x, jl = tid / TK, kl = tid % TK;
+  const real gamma = (real)kp.gamma, pfl = (real)kp.p_floor, rfl = (real)kp.rho_floor;
+  const int nb0 = kp.nb[0], nb1 = kp.nb[1], nb2 = kp.nb[2];
+  const int P1 = kp.P[1], P2 = kp.P[2];
+  const size_t plane = (size_t)P1 * P2, vstride = (size_t)kp.P[0] * plane, bstride = NVAR * vstride;
+  const int per_block = sl.tiles_j * sl.tiles_k * sl.segs;
+  const int nwork = sl.nlist * per_block;
+  const bool spherical = kp.geometry == 0;
+  const real Om = (real)kp.omega, Cd = (real)kp.cd;
+
+  // reflux face buffer layout (per slot): faces in order r-lo, r-hi, th-lo,
+  // th-hi, ph-lo, ph-hi; each [v][t1][t2]
+  const int fc0 = nb1 * nb2, fc1 = nb0 * nb2, fc2 = nb0 * nb1;
+  const size_t fstride = (size_t)NVAR * 2 * (fc0 + fc1 + fc2);
+
+  double inv_acc = 0.0;
+  long long hits = 0;
+  int cur_member = -1;
+
+  for (int w = blockIdx.x; w < nwork; w += gridDim.x) {
+    int li = w / per_block, rem = w - li * per_block;
+    const int seg = rem % sl.segs;
+    rem /= sl.segs;
+    const int tk = rem % sl.tiles_k, tj = rem / sl.tiles_k;
+    const int slot = sl.list[li];
+    const DevBlock B = kp.blk[slot];
+    const double dtm = kp.dt_used[B.member];
+    if (!(dtm > 0.0)) continue;  // member has reached its stop time (uniform)
+    if (S2 && B.member != cur_member) {
+      flush_acc(kp, inv_acc, cur_member, hits);
+      cur_member = B.member;
+    }
+    const real dt = (real)(dtm * sl.dtfac);
+    const LevelGeo<real> &G = GeoSel<real>::get(kp.geo, B.level);
+    const int j0 = tj * TJ, k0 = tk * TK;
+    const int nvj = min(TJ, nb1 - j0), nvk = min(TK, nb2 - k0);
+    const int ib = seg * sl.seg_len, ie = min(nb0, ib + sl.seg_len);
+    const int I0 = B.ix[0] * nb0, J0 = B.ix[1] * nb1 + j0, K0 = B.ix[2] * nb2 + k0;
+    const real *Uin = reinterpret_cast<const real *>(sl.Uin) + (size_t)slot * bstride;
+    const real *U0 = reinterpret_cast<const real *>(sl.U0) + (size_t)slot * bstride;
+    real *Uout = reinterpret_cast<real *>(sl.Uout) + (size_t)slot * bstride;
+    const bool valid = jl < nvj && kl < nvk;
+    const int j = j0 + jl, k = k0 + kl;           // interior indices in the block
+    const int J = J0 + jl, K = K0 + kl;           // global indices at the level
+
+    auto load_plane = [&](int p) {
+      real *dst = ring + ((p + 5) % 5) * NVAR * RP;
+      const real *src = Uin + (size_t)(p + NGH) * plane;
+      for (int q = tid; q < RP; q += NT) {
+        const int jj = q / RK, kk = q - (q / RK) * RK;
+        const int pj = j0 + jj, pk = k0 + kk;
+        if (pj < P1 && pk < P2) {
+          real u[NVAR], wv[NVAR];
+#pragma unroll
+          for (int v = 0; v < NVAR; v++) u[v] = src[v * vstride + (size_t)pj * P2 + pk];
+          cons2prim<real>(u, wv, gamma, pfl);
+#pragma unroll
+          for (int v = 0; v < NVAR; v++) dst[v * RP + q] = wv[v];
+        }
+      }
+    };
+    auto ringp = [&](int p) -> const real * { return ring + ((p + 5) % 5) * NVAR * RP; };
+    auto gather = [&](const real *pl, int jj, int kk, real *w) {
+#pragma unroll
+      for (int v = 0; v < NVAR; v++) w[v] = pl[v * RP + jj * RK + kk];
+    };
+    auto rflux = [&](int p, real *F) {  // face between planes p-1 and p
+      real a[NVAR], b[NVAR], c[NVAR], e[NVAR];
+      gather(ringp(p - 2), jl + 2, kl + 2, a);
+      gather(ringp(p - 1), jl + 2, kl + 2, b);
+      gather(ringp(p), jl + 2, kl + 2, c);
+      gather(ringp(p + 1), jl + 2, kl + 2, e);
+      tvdlf_face<real, 0>(a, b, c, e, gamma, F);
+    };
+    // div B at plane p on the (TJ+2) x (TK+2) positions around the tile
+    auto divb_plane = [&](int p) {
+      real *dst = dring + (p & 3) * DP;
+      const real *pm = ringp(p - 1), *pc = ringp(p), *pp = ringp(p + 1);
+      const int I = I0 + p;
+      const real rcm = G.rc[I - 1 + NGH], rcc = G.rc[I + NGH], rcp = G.rc[I + 1 + NGH];
+      for (int q = tid; q < DP; q += NT) {
+        const int dj = q / DK - 1, dk = q - (q / DK) * DK - 1;
+        if (dj > nvj || dk > nvk) continue;
+        const int jj = dj + 2, kk = dk + 2;
+        const int Jg = J0 + dj, Kg = K0 + dk;
+        const real brm = pm[5 * RP + jj * RK + kk], brp = pp[5 * RP + jj * RK + kk];
+        const real btm = pc[6 * RP + (jj - 1) * RK + kk], btp = pc[6 * RP + (jj + 1) * RK + kk];
+        const real bpm = pc[7 * RP + jj * RK + kk - 1], bpp = pc[7 * RP + jj * RK + kk + 1];
+        const real tcm = G.tc[Jg - 1 + NGH], tcp = G.tc[Jg + 1 + NGH];
+        const real pcm = G.pc[Kg - 1 + NGH], pcp = G.pc[Kg + 1 + NGH];
+        real div;
+        if (spherical) {
+          const real stc = G.sintc[Jg + NGH];
+          const real sm = G.sintc[Jg - 1 + NGH], sp = G.sintc[Jg + 1 + NGH];
+          div = (rcp * rcp * brp - rcm * rcm * brm) / (rcc * rcc * (rcp - rcm)) +
+                (sp * btp - sm * btm) / (rcc * stc * (tcp - tcm)) + (bpp - bpm) / (rcc * stc * (pcp - pcm));
+        } else {
+          div = (brp - brm) / (rcp - rcm) + (btp - btm) / (tcp - tcm) + (bpp - bpm) / (pcp - pcm);
+        }
+        dst[q] = div;
+      }
+    };
+
+    // ---- prologue: planes ib-2 .. ib+1 ----
+    for (int p = ib - 2; p <= ib + 1; p++) load_plane(p);
+    __syncthreads();
+    if (S2) {
+      divb_plane(ib - 1);
+      divb_plane(ib);
+    }
+    real Flo[NVAR];
+    if (valid) rflux(ib, Flo);
+
+    for (int i = ib; i < ie; i++) {
+      load_plane(i + 2);
+      __syncthreads();
+      if (S2) divb_plane(i + 1);
+      real Fhi[NVAR];
+      if (valid) rflux(i + 1, Fhi);
+      // theta and phi faces of plane i
+      {
+        const real *pl = ringp(i);
+        constexpr int NTH = (TJ + 1) * TK, NPH = TJ * (TK + 1);
+        for (int f = tid; f < NTH + NPH; f += NT) {
+          real a[NVAR], b[NVAR], c[NVAR], e[NVAR], F[NVAR];
+          if (f < NTH) {
+            const int row = f / TK, col = f - (f / TK) * TK;
+            if (row <= nvj && col < nvk) {
+              gather(pl, row, col + 2, a);
+              gather(pl, row + 1, col + 2, b);
+              gather(pl, row + 2, col + 2, c);
+              gather(pl, row + 3, col + 2, e);
+              tvdlf_face<real, 1>(a, b, c, e, gamma, F);
+#pragma unroll
+              for (int v = 0; v < NVAR; v++) fth[(v * (TJ + 1) + row) * TK + col] = F[v];
+            }
+          } else {
+            const int g = f - NTH, row = g / (TK + 1), col = g - (g / (TK + 1)) * (TK + 1);
+            if (row < nvj && col <= nvk) {
+              gather(pl, row + 2, col, a);
+              gather(pl, row + 2, col + 1, b);
+              gather(pl, row + 2, col + 2, c);
+              gather(pl, row + 2, col + 3, e);
+              tvdlf_face<real, 2>(a, b, c, e, gamma, F);
+#pragma unroll
+              for (int v = 0; v < NVAR; v++) fph[(v * TJ + row) * (TK + 1) + col] = F[v];
+            }
+          }
+        }
+      }
+      __syncthreads();
+      if (valid) {
+        const int I = I0 + i;
+        const int iI = I + NGH, iJ = J + NGH;
+        const real dphi = G.dphi;
+        const real dcos = G.dcos[iJ], dr2 = G.dr2[iI];
+        const real Arm = G.r2f[iI] * dcos * dphi, Arp = G.r2f[iI + 1] * dcos * dphi;
+        const real Atm = G.sinf[iJ] * dr2 * dphi, Atp = G.sinf[iJ + 1] * dr2 * dphi;
+        const real Ap = dr2 * G.dth[iJ];
+        const real V = G.dr3[iI] * dcos * dphi;
+        const real iV = real(1) / V;
+        real w[NVAR];
+        gather(ringp(i), jl + 2, kl + 2, w);
+        real un[NVAR];
+        const size_t cidx = (size_t)(i + NGH) * plane + (size_t)(j + NGH) * P2 + (k + NGH);
+#pragma unroll
+        for (int v = 0; v < NVAR; v++) {
+          const real ftl = fth[(v * (TJ + 1) + jl) * TK + kl], fth_ = fth[(v * (TJ + 1) + jl + 1) * TK + kl];
+          const real fpl = fph[(v * TJ + jl) * (TK + 1) + kl], fph_ = fph[(v * TJ + jl) * (TK + 1) + kl + 1];
+          const real div = (Arp * Fhi[v] - Arm * Flo[v]) + (Atp * fth_ - Atm * ftl) + Ap * (fph_ - fpl);
+          un[v] = -div * iV;
+        }
+        if (spherical) {
+          const real gr = (Arp - Arm) * iV, gt = (Atp - Atm) * iV, ir = real(0.5) * gr;
+          const real rho = w[0], vr = w[1], vt = w[2], vp = w[3], Br = w[5], Bt = w[6], Bp = w[7];
+          const real pt = w[4] + real(0.5) * (Br * Br + Bt * Bt + Bp * Bp);
+          un[1] += (rho * (vt * vt + vp * vp) - (Bt * Bt + Bp * Bp)) * ir + pt * gr;
+          un[2] += (-rho * vr * vt + Br * Bt) * ir + (rho * vp * vp - Bp * Bp) * gt + pt * gt;
+          un[3] += (-rho * vr * vp + Br * Bp) * ir - (rho * vt * vp - Bt * Bp) * gt;
+          un[6] += (vr * Bt - vt * Br) * ir;
+          un[7] += (vr * Bp - vp * Br) * ir + (vt * Bp - vp * Bt) * gt;
+          const real rc = G.rc[iI], st = G.sintc[iJ], ct = G.costc[iJ];
+          const real vs = vr * st + vt * ct;
+          un[1] += rho * (real(2) * Om * vp * st + Om * Om * rc * st * st);
+          un[2] += rho * (real(2) * Om * vp * ct + Om * Om * rc * st * ct);
+          un[3] += real(-2) * Om * rho * vs;
+          un[4] += rho * Om * Om * rc * st * vs;
+        }
+#pragma unroll
+        for (int v = 0; v < NVAR; v++) un[v] = U0[v * vstride + cidx] + dt * un[v];
+        if (S2 && Cd > real(0)) {
+          const real *dm = dring + ((i - 1) & 3) * DP, *dc = dring + (i & 3) * DP, *dp = dring + ((i + 1) & 3) * DP;
+          const int q = (jl + 1) * DK + (kl + 1);
+          const real rcm = G.rc[iI - 1], rcc = G.rc[iI], rcp = G.rc[iI + 1];
+          const real tcm = G.tc[iJ - 1], tcp = G.tc[iJ + 1];
+          const real pcm = G.pc[K - 1 + NGH], pcp = G.pc[K + 1 + NGH];
+          const real dr = G.dr[iI], dth = G.dth[iJ];
+          real gr_, gt_, gp_, h2inv;
+          if (spherical) {
+            const real st = G.sintc[iJ];
+            gr_ = (dp[q] - dm[q]) / (rcp - rcm);
+            gt_ = (dc[q + DK] - dc[q - DK]) / (rcc * (tcp - tcm));
+            gp_ = (dc[q + 1] - dc[q - 1]) / (rcc * st * (pcp - pcm));
+            const real xt = rcc * dth, xp = rcc * st * dphi;
+            h2inv = real(1) / (dr * dr) + real(1) / (xt * xt) + real(1) / (xp * xp);
+          } else {
+            gr_ = (dp[q] - dm[q]) / (rcp - rcm);
+            gt_ = (dc[q + DK] - dc[q - DK]) / (tcp - tcm);
+            gp_ = (dc[q + 1] - dc[q - 1]) / (pcp - pcm);
+            h2inv = real(1) / (dr * dr) + real(1) / (dth * dth) + real(1) / (dphi * dphi);
+          }
+          const real f = Cd / h2inv;
+          const real dB0 = f * gr_, dB1 = f * gt_, dB2 = f * gp_;
+          un[5] += dB0;
+          un[6] += dB1;
+          un[7] += dB2;
+          un[4] += w[5] * dB0 + w[6] * dB1 + w[7] * dB2;
+        }
+        hits += apply_floors<real>(un, gamma, pfl, rfl);
+        if (!(un[0] == un[0]) || !(un[4] == un[4])) atomicOr(kp.status, ST_NAN);
+#pragma unroll
+        for (int v = 0; v < NVAR; v++) Uout[v * vstride + cidx] = un[v];
+        if (S2) {
+          // CFL contribution of the new state (cells next to a finer face are
+          // left to the reflux, which changes them once more)
+          const bool skip = (i == 0 && B.nbr[0] == NB_FINER) || (i == nb0 - 1 && B.nbr[1] == NB_FINER) ||
+                            (j == 0 && B.nbr[2] == NB_FINER) || (j == nb1 - 1 && B.nbr[3] == NB_FINER) ||
+                            (k == 0 && B.nbr[4] == NB_FINER) || (k == nb2 - 1 && B.nbr[5] == NB_FINER);
+          if (!skip) {
+            real wn[NVAR];
+            cons2prim<real>(un, wn, gamma, pfl);
+            real dx0 = G.dr[iI], dx1 = G.dth[iJ], dx2 = G.dphi;
+            if (spherical) {
+              dx1 *= G.rc[iI];
+              dx2 *= G.rc[iI] * G.sintc[iJ];
+            }
+            const real s = (RT<real>::abs_(wn[1]) + fast_speed<real, 0>(wn, gamma)) / dx0 +
+                           (RT<real>::abs_(wn[2]) + fast_speed<real, 1>(wn, gamma)) / dx1 +
+                           (RT<real>::abs_(wn[3]) + fast_speed<real, 2>(wn, gamma)) / dx2;
+            inv_acc = fmax(inv_acc, (double)s);
+          }
+          if (sl.flux) {
+            real *fb = reinterpret_cast<real *>(sl.flux) + (size_t)slot * fstride;
+            // r faces
+            if (i == 0 && (B.nbr[0] == NB_COARSER || B.nbr[0] == NB_FINER))
+#pragma unroll
+              for (int v = 0; v < NVAR; v++) fb[(size_t)v * fc0 + j * nb2 + k] = Arm * Flo[v];
+            if (i == nb0 - 1 && (B.nbr[1] == NB_COARSER || B.nbr[1] == NB_FINER))
+#pragma unroll
+              for (int v = 0; v < NVAR; v++) fb[(size_t)NVAR * fc0 + (size_t)v * fc0 + j * nb2 + k] = Arp * Fhi[v];
+            const size_t o2 = (size_t)2 * NVAR * fc0, o4 = o2 + (size_t)2 * NVAR * fc1;
+            if (j == 0 && (B.nbr[2] == NB_COARSER || B.nbr[2] == NB_FINER))
+#pragma unroll
+              for (int v = 0; v < NVAR; v++)
+                fb[o2 + (size_t)v * fc1 + i * nb2 + k] = Atm * fth[(v * (TJ + 1) + jl) * TK + kl];
+            if (j == nb1 - 1 && (B.nbr[3] == NB_COARSER || B.nbr[3] == NB_FINER))
+#pragma unroll
+              for (int v = 0; v < NVAR; v++)
+                fb[o2 + (size_t)NVAR * fc1 + (size_t)v * fc1 + i * nb2 + k] = Atp * fth[(v * (TJ + 1) + jl + 1) * TK + kl];
+            if (k == 0 && (B.nbr[4] == NB_COARSER || B.nbr[4] == NB_FINER))
+#pragma unroll
+              for (int v = 0; v < NVAR; v++)
+                fb[o4 + (size_t)v * fc2 + i * nb1 + j] = Ap * fph[(v * TJ + jl) * (TK + 1) + kl];
+            if (k == nb2 - 1 && (B.nbr[5] == NB_COARSER || B.nbr[5] == NB_FINER))
+#pragma unroll
+              for (int v = 0; v < NVAR; v++)
+                fb[o4 + (size_t)NVAR * fc2 + (size_t)v * fc2 + i * nb1 + j] = Ap * fph[(v * TJ + jl) * (TK + 1) + kl + 1];
+          }
+        }
+#pragma unroll
+        for (int v = 0; v < NVAR; v++) Flo[v] = Fhi[v];
+      }
+    }
+    __syncthreads();  // shared memory is reused by the next work item
+  }
+  if (S2) flush_acc(kp, inv_acc, cur_member, hits);
+  else {
+    long long h = hits;
+    for (int o = 16; o > 0; o >>= 1) h += __shfl_xor_sync(0xffffffffu, h, o);
+    if ((threadIdx.x & 31) == 0 && h) atomicAdd(kp.floor_hits, (unsigned long long)h);
+  }
+}
+
+template <typename real, int TJ, int TK>
+int launch_t(const KParams &kp, const StageLaunch &sl, cudaStream_t s) {
+  const size_t smem = StageSmem<real>::bytes(TJ, TK);
+  static bool configured[2] = {false, false};
+  if (!configured[0]) {
+    cudaFuncSetAttribute(k_stage<real, TJ, TK, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaFuncSetAttribute(k_stage<real, TJ, TK, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    configured[0] = true;
+  }
+  if (sl.stage2)
+    k_stage<real, TJ, TK, true><<<sl.grid, TJ * TK, smem, s>>>(kp, sl);
+  else
+    k_stage<real, TJ, TK, false><<<sl.grid, TJ * TK, smem, s>>>(kp, sl);
+  return cudaPeekAtLastError() == cudaSuccess ? 0 : -1;
+}
+
+template <typename real>
+int dispatch(const KParams &kp, const StageLaunch &sl, cudaStream_t s) {
+  if (sl.tile_j == 8 && sl.tile_k == 8) return launch_t<real, 8, 8>(kp, sl, s);
+  if (sl.tile_j == 12 && sl.tile_k == 12) return launch_t<real, 12, 12>(kp, sl, s);
+  if (sl.tile_j == 8 && sl.tile_k == 32) return launch_t<real, 8, 32>(kp, sl, s);
+  if (sl.tile_j == 4 && sl.tile_k == 32) return launch_t<real, 4, 32>(kp, sl, s);
+  return -2;
+}
+
+template <typename real, int TJ, int TK>
+int occupancy_t() {
+  int n = 0;
+  const size_t smem = StageSmem<real>::bytes(TJ, TK);
+  cudaFuncSetAttribute(k_stage<real, TJ, TK, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  cudaFuncSetAttribute(k_stage<real, TJ, TK, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_stage<real, TJ, TK, true>, TJ * TK, smem) != cudaSuccess)
+    return 1;
+  return n > 0 ? n : 1;
+}
+
+template <typename real>
+int occupancy(int tj, int tk) {
+  if (tj == 8 && tk == 8) return occupancy_t<real, 8, 8>();
+  if (tj == 12 && tk == 12) return occupancy_t<real, 12, 12>();
+  if (tj == 8 && tk == 32) return occupancy_t<real, 8, 32>();
+  if (tj == 4 && tk == 32) return occupancy_t<real, 4, 32>();
+  return 1;
+}
+
+}  // namespace
+
+int stage_tile_supported(int precision, int tj, int tk) {
+  (void)precision;
+  return (tj == 8 && tk == 8) || (tj == 12 && tk == 12) || (tj == 8 && tk == 32) || (tj == 4 && tk == 32);
+}
+
+size_t stage_smem_bytes(int precision, int tj, int tk) {
+  return precision ? StageSmem<float>::bytes(tj, tk) : StageSmem<double>::bytes(tj, tk);
+}
+
+int stage_max_ctas_per_sm(int precision, int tj, int tk) {
+  return precision ? occupancy<float>(tj, tk) : occupancy<double>(tj, tk);
+}
+
+int stage_launch(const KParams &kp, const StageLaunch &sl, int precision, cudaStream_t s) {
+  if (sl.nlist <= 0) return 0;
+  return precision ? dispatch<float>(kp, sl, s) : dispatch<double>(kp, sl, s);
+}

@@ -1,0 +1,179 @@
+// Device-side ideal-MHD building blocks (templated on the working precision).
+//
+// Method (arXiv 2211.12867, Sect. 2.1): ideal MHD solved in the frame
+// co-rotating with the Sun with the TVDLF scheme and the Woodward limiter.
+// The limiter is the monotonised-central slope applied to the primitive
+// variables in index space; a face whose reconstructed density or pressure is
+// not positive falls back to the cell values; the TVDLF flux is
+// F = (F_L + F_R)/2 - c_max (U_R - U_L)/2 with c_max the larger |v_n| + c_f of
+// the two face states; the normal magnetic flux is zero.
+#pragma once
+#include "icarus_internal.h"
+
+template <typename real> struct RT;
+template <> struct RT<double> {
+  static __device__ __forceinline__ double sqrt_(double x) { return sqrt(x); }
+  static __device__ __forceinline__ double abs_(double x) { return fabs(x); }
+  static __device__ __forceinline__ double min_(double a, double b) { return fmin(a, b); }
+  static __device__ __forceinline__ double max_(double a, double b) { return fmax(a, b); }
+};
+template <> struct RT<float> {
+  static __device__ __forceinline__ float sqrt_(float x) { return sqrtf(x); }
+  static __device__ __forceinline__ float abs_(float x) { return fabsf(x); }
+  static __device__ __forceinline__ float min_(float a, float b) { return fminf(a, b); }
+  static __device__ __forceinline__ float max_(float a, float b) { return fmaxf(a, b); }
+};
+
+// Pressure from conserved variables.  In the mixed-precision mode the FP32
+// result is replaced by an FP64 recomputation from the same (FP32-stored)
+// conserved variables where the thermal energy is a small remainder of the
+// total: p < 0.05 e or plasma beta = p / (B^2/2) < 0.1.
+template <typename real>
+__device__ __forceinline__ real pressure_of(const real *u, real gamma) {
+  real ir = real(1) / u[0];
+  real msq = u[1] * u[1] + u[2] * u[2] + u[3] * u[3];
+  real me = real(0.5) * (u[5] * u[5] + u[6] * u[6] + u[7] * u[7]);
+  real p = (gamma - real(1)) * (u[4] - real(0.5) * msq * ir - me);
+  return p;
+}
+
+template <>
+__device__ __forceinline__ float pressure_of<float>(const float *u, float gamma) {
+  float ir = 1.0f / u[0];
+  float msq = u[1] * u[1] + u[2] * u[2] + u[3] * u[3];
+  float me = 0.5f * (u[5] * u[5] + u[6] * u[6] + u[7] * u[7]);
+  float p = (gamma - 1.0f) * (u[4] - 0.5f * msq * ir - me);
+  if (p < 0.05f * u[4] || p < 0.1f * me) {
+    double r = u[0], m1 = u[1], m2 = u[2], m3 = u[3], e = u[4], b1 = u[5], b2 = u[6], b3 = u[7];
+    double ms = m1 * m1 + m2 * m2 + m3 * m3;
+    double bs = b1 * b1 + b2 * b2 + b3 * b3;
+    double pd = ((double)gamma - 1.0) * (e - 0.5 * ms / r - 0.5 * bs);
+    p = (float)pd;
+  }
+  return p;
+}
+
+// U -> W with the pressure floor of the stage operator.
+template <typename real>
+__device__ __forceinline__ void cons2prim(const real *u, real *w, real gamma, real pfloor) {
+  real ir = real(1) / u[0];
+  w[0] = u[0];
+  w[1] = u[1] * ir;
+  w[2] = u[2] * ir;
+  w[3] = u[3] * ir;
+  real p = pressure_of<real>(u, gamma);
+  w[4] = p < pfloor ? pfloor : p;
+  w[5] = u[5];
+  w[6] = u[6];
+  w[7] = u[7];
+}
+
+template <typename real>
+__device__ __forceinline__ void prim2cons(const real *w, real *u, real gamma) {
+  real v2 = w[1] * w[1] + w[2] * w[2] + w[3] * w[3];
+  real b2 = w[5] * w[5] + w[6] * w[6] + w[7] * w[7];
+  u[0] = w[0];
+  u[1] = w[0] * w[1];
+  u[2] = w[0] * w[2];
+  u[3] = w[0] * w[3];
+  u[4] = w[4] / (gamma - real(1)) + real(0.5) * w[0] * v2 + real(0.5) * b2;
+  u[5] = w[5];
+  u[6] = w[6];
+  u[7] = w[7];
+}
+
+// fast magnetosonic speed along direction D
+template <typename real, int D>
+__device__ __forceinline__ real fast_speed(const real *w, real gamma) {
+  real ir = real(1) / w[0];
+  real a2 = gamma * w[4] * ir;
+  real b2 = (w[5] * w[5] + w[6] * w[6] + w[7] * w[7]) * ir;
+  real bn2 = w[5 + D] * w[5 + D] * ir;
+  real s = a2 + b2;
+  real disc = s * s - real(4) * a2 * bn2;
+  disc = disc < real(0) ? real(0) : disc;
+  return RT<real>::sqrt_(real(0.5) * (s + RT<real>::sqrt_(disc)));
+}
+
+template <typename real>
+__device__ __forceinline__ real mc_slope(real um, real u0, real up) {
+  real dm = u0 - um, dp = up - u0;
+  real dc = real(0.5) * (dm + dp);
+  real lim = RT<real>::min_(real(2) * RT<real>::abs_(dm), real(2) * RT<real>::abs_(dp));
+  lim = RT<real>::min_(lim, RT<real>::abs_(dc));
+  real s = dc > real(0) ? lim : -lim;
+  return dm * dp > real(0) ? s : real(0);
+}
+
+// physical flux along D from primitives (and the energy density e)
+template <typename real, int D>
+__device__ __forceinline__ void phys_flux(const real *w, real e, real *F) {
+  real vn = w[1 + D], Bn = w[5 + D];
+  real b2 = w[5] * w[5] + w[6] * w[6] + w[7] * w[7];
+  real pt = w[4] + real(0.5) * b2;
+  real vB = w[1] * w[5] + w[2] * w[6] + w[3] * w[7];
+  real rvn = w[0] * vn;
+  F[0] = rvn;
+#pragma unroll
+  for (int c = 0; c < 3; c++) {
+    F[1 + c] = rvn * w[1 + c] - w[5 + c] * Bn;
+    F[5 + c] = vn * w[5 + c] - Bn * w[1 + c];
+  }
+  F[1 + D] += pt;
+  F[5 + D] = real(0);
+  F[4] = (e + pt) * vn - Bn * vB;
+}
+
+// TVDLF face flux from the four cells a, b | c, e around the face (primitive
+// variables); F receives the numerical flux.
+template <typename real, int D>
+__device__ __forceinline__ void tvdlf_face(const real *a, const real *b, const real *c, const real *e,
+                                           real gamma, real *F) {
+  real WL[NVAR], WR[NVAR];
+#pragma unroll
+  for (int v = 0; v < NVAR; v++) {
+    WL[v] = b[v] + real(0.5) * mc_slope<real>(a[v], b[v], c[v]);
+    WR[v] = c[v] - real(0.5) * mc_slope<real>(b[v], c[v], e[v]);
+  }
+  if (!(WL[0] > real(0)) || !(WL[4] > real(0)) || !(WR[0] > real(0)) || !(WR[4] > real(0))) {
+#pragma unroll
+    for (int v = 0; v < NVAR; v++) {
+      WL[v] = b[v];
+      WR[v] = c[v];
+    }
+  }
+  real UL[NVAR], UR[NVAR], FL[NVAR], FR[NVAR];
+  prim2cons<real>(WL, UL, gamma);
+  prim2cons<real>(WR, UR, gamma);
+  phys_flux<real, D>(WL, UL[4], FL);
+  phys_flux<real, D>(WR, UR[4], FR);
+  real cl = RT<real>::abs_(WL[1 + D]) + fast_speed<real, D>(WL, gamma);
+  real cr = RT<real>::abs_(WR[1 + D]) + fast_speed<real, D>(WR, gamma);
+  real cm = cl > cr ? cl : cr;
+#pragma unroll
+  for (int v = 0; v < NVAR; v++) F[v] = real(0.5) * (FL[v] + FR[v]) - real(0.5) * cm * (UR[v] - UL[v]);
+  F[5 + D] = real(0);
+}
+
+// floors on a freshly updated cell; returns the number of floor hits
+template <typename real>
+__device__ __forceinline__ int apply_floors(real *u, real gamma, real pfloor, real rfloor) {
+  int hits = 0;
+  if (u[0] < rfloor) {
+    u[0] = rfloor;
+    hits++;
+  }
+  real p = pressure_of<real>(u, gamma);
+  if (p < pfloor) {
+    real ke = real(0.5) * (u[1] * u[1] + u[2] * u[2] + u[3] * u[3]) / u[0];
+    real me = real(0.5) * (u[5] * u[5] + u[6] * u[6] + u[7] * u[7]);
+    u[4] = pfloor / (gamma - real(1)) + ke + me;
+    hits++;
+  }
+  return hits;
+}
+
+// atomic max of a non-negative double through its bit pattern
+__device__ __forceinline__ void atomic_max_pos(unsigned long long *addr, double v) {
+  atomicMax(addr, (unsigned long long)__double_as_longlong(v));
+}

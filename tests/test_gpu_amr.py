@@ -1,0 +1,117 @@
+"""AMR on the GPU against the oracle: block trees and leaf order bit-exact
+given the same flags, conservative regrid data, multi-level stepping with
+reflux, and refinement flags bit-exact on the same stored state."""
+import math
+
+import numpy as np
+import pytest
+
+import oracle as O
+from gpu_common import make_pair, rel_linf, wind_setup
+from paper_2211_12867_gb300 import inputs as I
+
+pytestmark = pytest.mark.gpu
+STR = dict(x_min=(0.1, math.pi / 6, 0.0), x_max=(2.0, 5 * math.pi / 6, 2 * math.pi), stretch=True)
+
+
+def _pair(**kw):
+    args = dict(n=(24, 16, 32), nb=(8, 8, 8), max_level=3, max_blocks=4000, **STR)
+    args.update(kw)
+    g, o = make_pair(**args)
+    wind_setup(g, o)
+    return g, o
+
+
+def _regrid_both(g, o, flags):
+    g.set_flags(flags)
+    g.regrid()
+    o.regrid(flags)
+    assert np.array_equal(g.tree(0), o.tree())
+
+
+def test_tree_and_data_after_refinement():
+    g, o = _pair()
+    f = np.zeros(g.n_leaves(0), dtype=np.int8)
+    f[[0, 5, 9, 17, 22]] = 1
+    _regrid_both(g, o, f)
+    assert np.abs(g.sums(0) - o.sums()).max() / np.abs(o.sums()).max() < 1e-13
+    err = rel_linf(g.get_state(0), o.get_state())
+    assert err.max() < 1e-13, err
+    f = np.zeros(g.n_leaves(0), dtype=np.int8)
+    lv = g.tree(0)[:, 0]
+    f[np.where(lv == 2)[0][[0, 3, 11]]] = 1
+    _regrid_both(g, o, f)
+    assert 3 in g.tree(0)[:, 0]
+    assert o.balance_violations() == 0
+    err = rel_linf(g.get_state(0), o.get_state())
+    assert err.max() < 1e-13, err
+
+
+def test_multilevel_steps_with_reflux():
+    g, o = _pair()
+    f = np.zeros(g.n_leaves(0), dtype=np.int8)
+    f[[2, 7, 12, 20]] = 1
+    _regrid_both(g, o, f)
+    lv = g.tree(0)[:, 0]
+    f = np.zeros(g.n_leaves(0), dtype=np.int8)
+    f[np.where(lv == 2)[0][[1, 6]]] = 1
+    _regrid_both(g, o, f)
+    assert len(set(g.tree(0)[:, 0])) == 3
+    g.step(10)
+    o.advance(10)
+    err = rel_linf(g.get_state(0), o.get_state())
+    assert err.max() < 1e-10, err
+
+
+def test_coarsening_restores_families():
+    g, o = _pair()
+    _regrid_both(g, o, np.ones(g.n_leaves(0), dtype=np.int8))
+    g.step(2)
+    o.advance(2)
+    f = -np.ones(g.n_leaves(0), dtype=np.int8)
+    f[:8] = 0
+    _regrid_both(g, o, f)
+    err = rel_linf(g.get_state(0), o.get_state())
+    assert err.max() < 1e-10, err
+
+
+def test_conservation_across_levels_gpu():
+    g, o = make_pair(n=(16, 16, 16), nb=(8, 8, 8), max_level=2, omega=0.0, divb_cd=0.0, max_blocks=200,
+                     bc_lo=(2, 2, 0), bc_hi=(2, 2, 0), **STR)
+    W = np.zeros((g.n_leaves(0), 8) + g.block)
+    for n in range(g.n_leaves(0)):
+        W[n] = I.random_state(g.block, 300 + n, 1.5, v=0.3, b=0.3)
+        W[n, 0] = 1.0 + 0.2 * (W[n, 0] - 1.25)
+        W[n, 4] = 1.0 + 0.2 * (W[n, 4] - 1.25)
+    g.set_state(0, W, prim=True)
+    o.set_state(g.get_state(0))
+    f = np.zeros(g.n_leaves(0), dtype=np.int8)
+    f[[0, 3]] = 1
+    _regrid_both(g, o, f)
+    s0 = g.sums(0)
+    g.step(6)
+    s1 = g.sums(0)
+    for v in (0, 4):
+        assert abs(s1[v] - s0[v]) / abs(s0[v]) < 1e-13
+
+
+def test_flags_bit_exact_on_same_state():
+    g, o = _pair(max_level=3)
+    cme = dict(I.cme_config2(seed=1), t_start=0.0)
+    g.inject_cone_cme(0, **cme)
+    o.set_cme(**cme)
+    o.snapshot_vbg()
+    g.step(30)
+    o.set_state(g.get_state(0))
+    o.t = g.step(0)[0]
+    fg = g.flag_refine()
+    o.ghost_fill()
+    fo = o.flag()
+    assert np.array_equal(fg, fo)
+    assert (fg == 1).sum() > 0
+    # the same decision on both sides grows the same tree
+    _regrid_both(g, o, fg)
+    o.set_state(g.get_state(0))
+    fg = g.flag_refine()
+    o.ghost_fill()
+    assert np.array_equal(fg, o.flag())

@@ -1,0 +1,142 @@
+"""CUDA path against the FP64 oracle on the same seeded inputs.
+
+Bar (FP64 mode): max relative L-infinity error per variable <= 1e-10
+(normalised by each variable's largest magnitude).  The CUDA kernels contract
+multiply-adds and evaluate reciprocals differently from the oracle's plain C,
+so the two differ at the level of a few ulp per operation; 1e-10 leaves room
+for their growth over 200 steps (a 1e-15 perturbation of the 200-step run
+grows to <= 2e-14 in the oracle itself)."""
+import math
+
+import numpy as np
+import pytest
+
+import oracle as O
+from gpu_common import SPH, make_pair, rel_linf, wind_setup
+from paper_2211_12867_gb300 import inputs as I
+
+pytestmark = pytest.mark.gpu
+TOL = 1e-10
+
+
+def test_uniform_state_preserved_stretched():
+    g, o = make_pair(n=(24, 16, 16), nb=(8, 8, 8), stretch=True, omega=0.0,
+                     x_min=(0.1, math.pi / 6, 0.0), x_max=(2.0, 5 * math.pi / 6, 2 * math.pi),
+                     bc_lo=(1, 1, 0), bc_hi=(1, 1, 0))
+    W = np.zeros((g.n_leaves(0), 8) + g.block)
+    W[:, 0], W[:, 4] = 1.3, 0.7
+    g.set_state(0, W, prim=True)
+    U0 = g.get_state(0)
+    g.step(5)
+    U1 = g.get_state(0)
+    assert np.abs(U1 - U0).max() < 1e-13
+
+
+def test_first_step_matches_oracle():
+    g, o = make_pair(n=(60, 16, 32), nb=(12, 8, 8))
+    wind_setup(g, o)
+    assert abs(g.dt()[0] - o.compute_dt()) / o.compute_dt() < 1e-13
+    t = g.step(1)
+    o.advance(1)
+    assert abs(t[0] - o.t) < 1e-15
+    err = rel_linf(g.get_state(0), o.get_state())
+    assert err.max() < 1e-12, err
+
+
+def test_config1_200_steps_fp64():
+    """60 x 16 x 32 equidistant wedge, 0.1-1.1 AU, 12x8x8 blocks, CFL 0.8."""
+    g, o = make_pair(n=(60, 16, 32), nb=(12, 8, 8))
+    wind_setup(g, o)
+    t = g.step(200)
+    o.advance(200)
+    assert abs(t[0] - o.t) / o.t < 1e-12
+    err = rel_linf(g.get_state(0), o.get_state())
+    assert err.max() < TOL, err
+    w, hits = g.status()
+    assert w == 0
+
+
+def test_ragged_tiles_and_segments():
+    """blocks that the (theta, phi) tile and the radial segment do not divide"""
+    g, o = make_pair(n=(40, 20, 24), nb=(20, 10, 12))
+    wind_setup(g, o)
+    for tile, seg in (((8, 8), 6), ((4, 32), 7), ((12, 12), 0), ((8, 32), 3)):
+        g2, o2 = make_pair(n=(40, 20, 24), nb=(20, 10, 12))
+        wind_setup(g2, o2)
+        g2.set_tile(*tile, seg)
+        g2.step(3)
+        o2.advance(3)
+        err = rel_linf(g2.get_state(0), o2.get_state())
+        assert err.max() < 1e-12, (tile, seg, err)
+
+
+def test_graph_and_direct_launch_agree():
+    g1, _ = make_pair(n=(60, 16, 32), nb=(12, 8, 8))
+    g2, o = make_pair(n=(60, 16, 32), nb=(12, 8, 8))
+    wind_setup(g1, o)
+    wind_setup(g2, o)
+    g2.use_graph(False)
+    g1.step(7)
+    g2.step(7)
+    assert np.array_equal(g1.get_state(0), g2.get_state(0))
+
+
+def test_t_stop_clipping():
+    g, o = make_pair(n=(60, 16, 32), nb=(12, 8, 8))
+    wind_setup(g, o)
+    dt = g.dt()[0]
+    t_stop = 2.5 * dt
+    t = g.step(10, t_stop=t_stop)
+    assert t[0] == t_stop
+    o.advance(10, t_stop)
+    assert o.t == t_stop
+    err = rel_linf(g.get_state(0), o.get_state())
+    assert err.max() < 1e-12
+
+
+def test_cartesian_periodic_conservation_gpu():
+    g, o = make_pair(n=(16, 16, 16), nb=(8, 8, 8), geometry=1, x_min=(0, 0, 0), x_max=(1, 1, 1), omega=0.0,
+                     divb_cd=0.0, gamma=5 / 3, bc_lo=(0, 0, 0), bc_hi=(0, 0, 0))
+    W = np.zeros((g.n_leaves(0), 8) + g.block)
+    for n in range(g.n_leaves(0)):
+        W[n] = I.random_state(g.block, 100 + n, 5 / 3, v=0.3, b=0.3)
+    g.set_state(0, W, prim=True)
+    o.set_state(g.get_state(0))
+    s0 = g.sums(0)
+    g.step(10)
+    o.advance(10)
+    s1 = g.sums(0)
+    assert np.all(np.abs(s1 - s0) / (np.abs(s0) + 1.0) < 1e-13)
+    err = rel_linf(g.get_state(0), o.get_state())
+    assert err.max() < 1e-11, err
+
+
+def test_cone_cme_injection_parity():
+    g, o = make_pair(n=(60, 16, 32), nb=(12, 8, 8))
+    wind_setup(g, o)
+    cme = I.cme_config2(seed=3)
+    cme = dict(cme, t_start=0.0)
+    g.inject_cone_cme(0, **cme)
+    o.set_cme(**cme)
+    o.snapshot_vbg()
+    g.step(40)
+    o.advance(40)
+    err = rel_linf(g.get_state(0), o.get_state())
+    assert err.max() < TOL, err
+    # the CME plasma (1000 km/s) entered the domain: radial speed above the
+    # fastest wind (750 km/s)
+    U = g.get_state(0)
+    assert (U[:, 1] / U[:, 0]).max() > 8.5
+
+
+def test_probe_parity():
+    g, o = make_pair(n=(60, 16, 32), nb=(12, 8, 8))
+    wind_setup(g, o)
+    g.step(20)
+    o.advance(20)
+    rng = np.random.default_rng(5)
+    pts = np.stack([rng.uniform(0.12, 1.08, 64), rng.uniform(0.6, 2.5, 64), rng.uniform(0, 2 * np.pi, 64)], 1)
+    a, b = g.probe(0, pts), o.probe(pts)
+    assert np.allclose(a, b, rtol=1e-10, atol=1e-12)
+    out = g.probe(0, np.array([[5.0, 1.0, 1.0]]))
+    assert np.all(np.isnan(out))
