@@ -1,0 +1,332 @@
+"""Benchmark of the Icarus MHD update on GB300.
+
+Workload (N = 1): the 512 x 60 x 180 single-level spherical wedge over
+0.1-2 AU, +-60 deg, 360 deg, with the seeded inner-boundary wind and a cone
+CME (30 deg half width, 1000 km/s) being injected, in the FP32 mode with FP64
+pressure islands (or FP64 with --precision fp64).  A step is one full
+midpoint predictor-corrector step of every cell (ghost fills, two stage
+sweeps with cleaning, CFL reduction); the metric is cell-updates per second.
+
+Timed region: K steps replayed from the CUDA graph, bracketed by CUDA events
+on the library's stream (inputs resident in HBM; the state, 0.2-0.35 GB, is
+larger than L2).  A second pass of K steps with per-launch events gives the
+average duration of each kernel for the roofline of the dominant kernel.  The
+end-to-end figure drives the same K steps through the public API from pinned
+host buffers: the initial state uploaded, every step's stop times sent and
+member times read back, the Earth probe read back every step, the final state
+downloaded.
+
+--impl reference times the FP64 CPU oracle (test infrastructure, not the
+product) on a bounded sample of the same workload on the host cores.
+
+Multi-GPU (torchrun, N > 1): every rank runs an independent replica of the
+workload (weak scaling); ranks meet at barriers and the slowest rank's time
+is reported.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+from paper_2211_12867_gb300 import inputs as I  # noqa: E402
+
+N_CELLS = (512, 60, 180)
+BLOCK = (64, 60, 180)
+X_MIN = (0.1, math.pi / 6, 0.0)
+X_MAX = (2.0, 5 * math.pi / 6, 2 * math.pi)
+WORKLOAD = "wedge512x60x180_cme"
+BYTES_PER_CELL_STEP = {"f32": 160, "f64": 320}          # read U, write U*, read U*, read U, write U
+BYTES_PER_CELL_CORRECTOR = {"f32": 96, "f64": 192}       # read U*, read U, write U^{n+1}
+
+
+def parse():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=400)
+    p.add_argument("--warmup", type=int, default=10)
+    p.add_argument("--impl", default="icarus", choices=["icarus", "reference"])
+    p.add_argument("--precision", default="fp32", choices=["fp32", "fp64"])
+    p.add_argument("--no-tune", action="store_true")
+    p.add_argument("--cpu-seconds", type=float, default=12.0)
+    p.add_argument("--skip-cpu-baseline", action="store_true")
+    return p.parse_args()
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+class Clocks:
+    """nvidia-smi samples (200 ms) while the timed region runs."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except Exception:
+            self.proc = None
+        time.sleep(0.3)
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 8:
+                continue
+            try:
+                sm.append(float(f[0]))
+                mx.append(float(f[1]))
+            except ValueError:
+                continue
+            for n, v in zip(names, f[4:8]):
+                if v.lower().startswith("active"):
+                    reasons.add(n)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"], "samples": 0}
+        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": float(max(mx)), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def setup_grid(precision, seed=0):
+    from paper_2211_12867_gb300.icarus import FP32_MIXED, FP64, Icarus
+    g = Icarus(n_cells=N_CELLS, block=BLOCK, x_min=X_MIN, x_max=X_MAX, omega=I.OMEGA, cfl=0.8, divb_cd=0.8,
+               precision=FP32_MIXED if precision == "fp32" else FP64)
+    wm = I.wind_map(N_CELLS[1], N_CELLS[2], X_MIN[1], X_MAX[1], seed=seed, r_in=X_MIN[0])
+    g.set_inner_boundary(0, wm)
+    rc = I.radial_centres(N_CELLS[0], X_MIN[0], X_MAX[0], 0)
+    G = I.initial_prim(wm, rc, X_MIN[0], 1.5, colat_min=X_MIN[1], colat_max=X_MAX[1])
+    W = I.global_to_blocks(G, g.tree(0), BLOCK)
+    g.set_state(0, W, prim=True)
+    cme = dict(I.cme_config2(seed=seed), t_start=0.0)
+    g.inject_cone_cme(0, **cme)
+    return g, W, wm, cme
+
+
+def roofline_traffic(prec_tag):
+    """DRAM traffic per corrector launch from the committed ncu summary, if it
+    was taken on the current stage-kernel source."""
+    path = os.path.join(ROOT, "profiles", "stage_corrector_traffic.json")
+    src = os.path.join(ROOT, "paper_2211_12867_gb300", "csrc", "k_stage.cu")
+    try:
+        with open(path) as f:
+            d = json.load(f)
+        h = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+        if d.get("k_stage_sha256_16") != h or d.get("precision") != prec_tag:
+            return None
+        return float(d["bytes_per_launch_full_workload"])
+    except Exception:
+        return None
+
+
+def cpu_baseline(seconds, precision_tag):
+    """Oracle (FP64, all host cores) on a bounded sample: the inner 64 radial
+    cells of the same wedge (64 x 60 x 180), same wind and start state."""
+    import oracle as O
+    n = (64, 60, 180)
+    r_out = X_MIN[0] + (X_MAX[0] - X_MIN[0]) * 64 / N_CELLS[0]
+    g = O.Grid(n=n, nb=(16, 12, 12), xmin=X_MIN, xmax=(r_out, X_MAX[1], X_MAX[2]), omega=I.OMEGA, cfl=0.8,
+               divb_cd=0.8)
+    wm = I.wind_map(n[1], n[2], X_MIN[1], X_MAX[1], seed=0)
+    g.set_boundary_map(wm)
+    rc = I.radial_centres(N_CELLS[0], X_MIN[0], X_MAX[0], 0)[:64]
+    G = I.initial_prim(wm, rc, X_MIN[0], 1.5, colat_min=X_MIN[1], colat_max=X_MAX[1])
+    g.set_state(I.global_to_blocks(G, g.tree(), (16, 12, 12)), prim=True)
+    g.set_cme(t_start=0.0, **I.cme_config2(seed=0))
+    cells = 64 * 60 * 180
+    t0 = time.perf_counter()
+    steps = 0
+    while True:
+        g.advance(1)
+        steps += 1
+        el = time.perf_counter() - t0
+        if el >= seconds:
+            break
+    return {"value": cells * steps / el, "unit": "cell-updates/s", "cores": O.max_threads(), "kind": "oracle",
+            "sample": f"{steps} step(s) of the inner 64x60x180 cells of the 512x60x180 wedge (FP64 oracle, "
+                      f"{el:.1f} s)"}
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    cb = cpu_baseline(max(5.0, args.cpu_seconds), "f64")
+    line = {"metric": "cell-updates/s", "value": cb["value"], "unit": "cell-updates/s", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": None, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "cells": int(np.prod(N_CELLS)), "sample": cb["sample"]},
+            "impl": "reference", "cpu_baseline": cb,
+            "e2e": {"value": cb["value"], "unit": "cell-updates/s", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return run_reference(args)
+    import torch
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    else:
+        torch.cuda.set_device(0)
+    prec_tag = "f32" if args.precision == "fp32" else "f64"
+    g, W0, wm, cme = setup_grid(args.precision, seed=rank)
+    tuned = None
+    if not args.no_tune:
+        from paper_2211_12867_gb300.autotune import tune
+        best, best_ms, _ = tune(g, steps=3)
+        tuned = {"tile": [best[0], best[1]], "r_segment": best[2], "ms": round(best_ms, 4)}
+    cells = int(np.prod(N_CELLS))
+    g.step(args.warmup, want_time=False)
+    g.stream.synchronize()
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    # ---- timed region: graph replay ----
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    barrier()
+    with Clocks(local) as clk:
+        e0.record(g.stream)
+        g.step(args.steps, want_time=False)
+        e1.record(g.stream)
+        e1.synchronize()
+    barrier()
+    ms = e0.elapsed_time(e1)
+    if dist is not None:
+        t = torch.tensor([ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    value = cells * args.steps * world / (ms / 1e3)
+    kps = g.kernels_per_step()
+
+    # ---- per-kernel durations (direct launches with event pairs) ----
+    g.profile(True)
+    g.profile_read()
+    p0, p1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    p0.record(g.stream)
+    g.step(args.steps, want_time=False)
+    p1.record(g.stream)
+    kms, kcnt = g.profile_read()
+    prof_step_ms = p0.elapsed_time(p1) / args.steps
+    g.profile(False)
+    from paper_2211_12867_gb300.icarus import PROFILE_KINDS
+    per_kernel = {k: {"launches": int(c), "avg_ms": (float(m) / c if c else None), "share": None}
+                  for k, m, c in zip(PROFILE_KINDS, kms, kcnt)}
+    tot = float(kms.sum())
+    for k, m in zip(PROFILE_KINDS, kms):
+        per_kernel[k]["share"] = float(m) / tot if tot > 0 else None
+    hbm, peak_kind = peaks()
+    corr_ms = per_kernel["stage_corrector"]["avg_ms"]
+    achieved = BYTES_PER_CELL_CORRECTOR[prec_tag] * cells / (corr_ms / 1e3) / 1e9
+    traffic = roofline_traffic(prec_tag)
+    roofline = {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s", "frac": achieved / hbm,
+                "traffic": traffic, "kernel": "k_stage (corrector)", "peak_source": peak_kind,
+                "algorithmic_bytes_per_cell": BYTES_PER_CELL_CORRECTOR[prec_tag],
+                "step_frac": BYTES_PER_CELL_STEP[prec_tag] * cells / (ms / args.steps / 1e3) / 1e9 / hbm,
+                "profiled_ms_per_step": prof_step_ms, "kernels": per_kernel}
+
+    # ---- end to end through the public API, host buffers ----
+    from paper_2211_12867_gb300.icarus import Icarus  # noqa: F401
+    pin_state = torch.empty(W0.size, dtype=torch.float64).pin_memory().numpy().reshape(W0.shape)
+    pin_state[...] = g.get_state(0)
+    pin_out = torch.empty(W0.size, dtype=torch.float64).pin_memory().numpy().reshape(W0.shape)
+    t_now = float(g.step(0)[0])
+    earth = I.earth_position(t_now, 0.0)
+    barrier()
+    w0 = time.perf_counter()
+    g.set_state(0, pin_state)                       # h2d: the job's input state
+    for s in range(args.steps):
+        g.step(1, t_stop=np.inf)                    # h2d t_stop, d2h member time
+        g.probe(0, earth[None, :])                  # h2d probe point, d2h 8 primitives
+    pin_out[...] = g.get_state(0)                   # d2h: the job's output state
+    torch.cuda.synchronize()
+    barrier()
+    e2e_s = time.perf_counter() - w0
+    if dist is not None:
+        t = torch.tensor([e2e_s], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_s = float(t.item())
+    state_bytes = W0.size * 8
+    e2e = {"value": cells * args.steps * world / e2e_s, "unit": "cell-updates/s",
+           "h2d_bytes_per_step": (state_bytes + args.steps * (8 + 24)) / args.steps,
+           "d2h_bytes_per_step": (state_bytes + args.steps * (8 + 64)) / args.steps}
+
+    word, floor_hits = g.status()
+    cb = None
+    if rank == 0 and not args.skip_cpu_baseline:
+        cb = cpu_baseline(args.cpu_seconds, prec_tag)
+    if rank == 0:
+        line = {"metric": "cell-updates/s", "value": value, "unit": "cell-updates/s", "n_gpus": world,
+                "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps,
+                "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": prec_tag,
+                "data": "synthetic",
+                "config": {"workload": WORKLOAD, "grid": list(N_CELLS), "block": list(BLOCK),
+                           "precision": "fp32+fp64-islands" if prec_tag == "f32" else "fp64",
+                           "cells": cells, "l2": "state > L2 (no flush needed)", "parallelism": f"replicas{world}",
+                           "tuned": tuned},
+                "roofline": roofline, "cpu_baseline": cb, "e2e": e2e, "gpu_launches": kps * args.steps,
+                "clocks": clk.summary(), "status_word": word, "floor_hits": floor_hits}
+        print(json.dumps(line), flush=True)
+    if dist is not None:
+        dist.barrier()
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -222,6 +222,18 @@ icarus_status icarus_use_graph(icarus_ctx *ctx, int enable);
  * accounting). */
 icarus_status icarus_kernels_per_step(icarus_ctx *ctx, int *n);
 
+/* Per-launch timing with CUDA events (enable = 1).  While enabled,
+ * icarus_step launches the kernels directly instead of replaying the graph
+ * and records an event pair around every launch on the context's stream. */
+icarus_status icarus_profile(icarus_ctx *ctx, int enable);
+
+/* Device time (ms) and number of launches per kernel kind accumulated since
+ * the previous read, then reset.  Kinds: 0 dt begin, 1 ghost fill from
+ * neighbours, 2 physical-boundary ghosts, 3 predictor stage, 4 corrector
+ * stage, 5 reflux, 6 dt finalize.  ms and count hold nkinds entries (<= 7).
+ * Synchronises the stream. */
+icarus_status icarus_profile_read(icarus_ctx *ctx, double *ms, int *count, int nkinds);
+
 void icarus_destroy(icarus_ctx *ctx);
 const char *icarus_status_string(icarus_status s);
 

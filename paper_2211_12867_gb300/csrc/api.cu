@@ -226,6 +226,11 @@ struct icarus_ctx {
   bool poisoned = false;
   std::vector<double> h_tstop;
   int kernels_per_step = 0;
+  // per-launch profiling
+  bool prof_on = false;
+  std::vector<cudaEvent_t> ev;
+  std::vector<int> ev_kind;   // kind of each event pair
+  size_t ev_used = 0;         // events recorded since the last read
 };
 
 namespace {
@@ -614,6 +619,19 @@ icarus_status build_geometry(icarus_ctx *c) {
 }
 
 // ---- launch sequence ----
+void prof_mark(icarus_ctx *c, int kind, int end) {
+  if (c->ev_used >= c->ev.size()) {
+    cudaEvent_t e;
+    if (cudaEventCreate(&e) != cudaSuccess) return;
+    c->ev.push_back(e);
+  }
+  if (!end) {
+    if (c->ev_used / 2 >= c->ev_kind.size()) c->ev_kind.resize(c->ev_used / 2 + 1);
+    c->ev_kind[c->ev_used / 2] = kind;
+  }
+  cudaEventRecord(c->ev[c->ev_used], c->stream);
+  c->ev_used++;
+}
 void default_tiles(icarus_ctx *c) {
   const int n1 = c->d.block[1], n2 = c->d.block[2];
   if (c->tile_j && c->tile_k) {
@@ -660,15 +678,31 @@ StageLaunch stage_cfg(icarus_ctx *c, int stage2) {
   return sl;
 }
 
+// optional event pair around a launch (profiling mode only)
+struct ProfScope {
+  icarus_ctx *c;
+  int kind;
+  ProfScope(icarus_ctx *c_, int k) : c(c_), kind(k) {
+    if (c->prof_on) prof_mark(c, kind, 0);
+  }
+  ~ProfScope() {
+    if (c->prof_on) prof_mark(c, kind, 1);
+  }
+};
+
 int enqueue_ghost(icarus_ctx *c, void *buf, double tfac) {
   int n = 0;
   for (int L = 1; L <= c->max_level_present; L++) {
     if (c->lvl_count[L] == 0) continue;
-    ghost_neighbour_launch(c->kp, buf, c->prec, c->lvl_list + c->lvl_start[L], c->lvl_count[L], c->shell,
-                           c->lay.nshell, L, c->stream);
+    {
+      ProfScope p(c, 1);
+      ghost_neighbour_launch(c->kp, buf, c->prec, c->lvl_list + c->lvl_start[L], c->lvl_count[L], c->shell,
+                             c->lay.nshell, L, c->stream);
+    }
     n++;
     for (int dd = 0; dd < 3; dd++) {
       if (c->side_count[L][dd] == 0) continue;
+      ProfScope p(c, 2);
       ghost_physical_launch(c->kp, buf, c->prec, c->sides + c->side_start[L][dd], c->side_count[L][dd], dd, L, tfac,
                             c->stream);
       n++;
@@ -679,7 +713,10 @@ int enqueue_ghost(icarus_ctx *c, void *buf, double tfac) {
 
 int enqueue_step(icarus_ctx *c) {
   int n = 0;
-  dt_begin_launch(c->kp, c->tstop, c->stream);
+  {
+    ProfScope p(c, 0);
+    dt_begin_launch(c->kp, c->tstop, c->stream);
+  }
   n++;
   n += enqueue_ghost(c, c->U, 0.0);
   StageLaunch s1 = stage_cfg(c, 0);
@@ -687,7 +724,10 @@ int enqueue_step(icarus_ctx *c) {
   s1.U0 = c->U;
   s1.Uout = c->Us;
   s1.flux = nullptr;
-  stage_launch(c->kp, s1, c->prec, c->stream);
+  {
+    ProfScope p(c, 3);
+    stage_launch(c->kp, s1, c->prec, c->stream);
+  }
   n++;
   n += enqueue_ghost(c, c->Us, 0.5);
   StageLaunch s2 = stage_cfg(c, 1);
@@ -695,13 +735,20 @@ int enqueue_step(icarus_ctx *c) {
   s2.U0 = c->U;
   s2.Uout = c->U;
   s2.flux = c->d.max_level > 1 ? c->flux : nullptr;
-  stage_launch(c->kp, s2, c->prec, c->stream);
+  {
+    ProfScope p(c, 4);
+    stage_launch(c->kp, s2, c->prec, c->stream);
+  }
   n++;
   if (c->nrlist > 0) {
+    ProfScope p(c, 5);
     reflux_launch(c->kp, c->U, c->flux, c->prec, c->rlist, c->nrlist, c->stream);
     n++;
   }
-  dt_finalize_launch(c->kp, c->d.cfl, c->stream);
+  {
+    ProfScope p(c, 6);
+    dt_finalize_launch(c->kp, c->d.cfl, c->stream);
+  }
   n++;
   return n;
 }
@@ -866,6 +913,7 @@ icarus_status icarus_init_grid(const icarus_grid_desc *desc, icarus_ctx **out) {
 void icarus_destroy(icarus_ctx *c) {
   if (!c) return;
   if (c->graph) cudaGraphExecDestroy(c->graph);
+  for (cudaEvent_t e : c->ev) cudaEventDestroy(e);
   delete c;
 }
 
@@ -963,7 +1011,7 @@ icarus_status icarus_step(icarus_ctx *c, int n_steps, const double *t_stop, doub
   c->h_tstop.assign(t_stop, t_stop + nm);
   CK(cudaMemcpyAsync(c->tstop, c->h_tstop.data(), sizeof(double) * nm, cudaMemcpyHostToDevice, c->stream));
   if (n_steps > 0) {
-    if (c->use_graph && c->stream != nullptr) {
+    if (c->use_graph && !c->prof_on && c->stream != nullptr) {
       if (!c->graph_valid) {
         if (c->graph) {
           cudaGraphExecDestroy(c->graph);
@@ -1277,6 +1325,33 @@ icarus_status icarus_regrid(icarus_ctx *c) {
   if (st != ICARUS_OK) return st;
   CK(cudaStreamSynchronize(c->stream));
   c->flags_valid = false;
+  return ICARUS_OK;
+}
+
+icarus_status icarus_profile(icarus_ctx *c, int enable) {
+  if (!c) return ICARUS_ERR_ARG;
+  c->prof_on = enable != 0;
+  c->ev_used = 0;
+  return ICARUS_OK;
+}
+
+icarus_status icarus_profile_read(icarus_ctx *c, double *ms, int *count, int nkinds) {
+  if (!c || !ms || !count || nkinds < 1 || nkinds > 7) return ICARUS_ERR_ARG;
+  CK(cudaStreamSynchronize(c->stream));
+  for (int k = 0; k < nkinds; k++) {
+    ms[k] = 0.0;
+    count[k] = 0;
+  }
+  for (size_t p = 0; p + 1 < c->ev_used; p += 2) {
+    float t = 0.0f;
+    CK(cudaEventElapsedTime(&t, c->ev[p], c->ev[p + 1]));
+    const int k = c->ev_kind[p / 2];
+    if (k < nkinds) {
+      ms[k] += t;
+      count[k]++;
+    }
+  }
+  c->ev_used = 0;
   return ICARUS_OK;
 }
 

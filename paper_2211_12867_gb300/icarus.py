@@ -34,7 +34,7 @@ EXPORTS = [
     "icarus_n_leaves", "icarus_get_tree", "icarus_set_state", "icarus_get_state", "icarus_set_time",
     "icarus_set_member_max_level", "icarus_ghost_fill", "icarus_conservation_sums", "icarus_get_dt",
     "icarus_status_word", "icarus_set_tile", "icarus_use_graph", "icarus_kernels_per_step",
-    "icarus_destroy", "icarus_status_string",
+    "icarus_profile", "icarus_profile_read", "icarus_destroy", "icarus_status_string",
 ]
 
 
@@ -103,6 +103,8 @@ def load(build_if_missing: bool = True):
             "icarus_set_tile": [P, I, I, I],
             "icarus_use_graph": [P, I],
             "icarus_kernels_per_step": [P, C.POINTER(I)],
+            "icarus_profile": [P, I],
+            "icarus_profile_read": [P, dp, C.POINTER(I), I],
         }
         for name, args in sig.items():
             f = getattr(L, name)
@@ -286,3 +288,18 @@ class Icarus:
         n = C.c_int(0)
         _chk("icarus_kernels_per_step", self.lib.icarus_kernels_per_step(self.ctx, C.byref(n)))
         return n.value
+
+    def profile(self, enable=True):
+        _chk("icarus_profile", self.lib.icarus_profile(self.ctx, int(bool(enable))))
+
+    def profile_read(self):
+        """(ms[7], count[7]) per kernel kind since the last read (see PROFILE_KINDS)."""
+        ms = np.zeros(7)
+        cnt = np.zeros(7, dtype=np.int32)
+        _chk("icarus_profile_read", self.lib.icarus_profile_read(self.ctx, _dp(ms),
+                                                                 cnt.ctypes.data_as(C.POINTER(C.c_int)), 7))
+        return ms, cnt
+
+
+PROFILE_KINDS = ["dt_begin", "ghost_neighbour", "ghost_physical", "stage_predictor", "stage_corrector",
+                 "reflux", "dt_finalize"]
