@@ -62,6 +62,8 @@ def parse():
     p.add_argument("--no-tune", action="store_true")
     p.add_argument("--cpu-seconds", type=float, default=12.0)
     p.add_argument("--skip-cpu-baseline", action="store_true")
+    p.add_argument("--mode", default="full", choices=["full", "kernel"],
+                   help="kernel: set up and run warmup + steps only (for profiler captures)")
     return p.parse_args()
 
 
@@ -231,6 +233,11 @@ def main():
     cells = int(np.prod(N_CELLS))
     g.step(args.warmup, want_time=False)
     g.stream.synchronize()
+    if args.mode == "kernel":
+        g.step(args.steps, want_time=False)
+        g.stream.synchronize()
+        print(json.dumps({"mode": "kernel", "steps": args.steps, "status": g.status()[0]}), flush=True)
+        return 0
 
     def barrier():
         if dist is not None:
