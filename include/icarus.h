@@ -203,6 +203,22 @@ icarus_status icarus_ghost_fill(icarus_ctx *ctx);
 /* Deterministic FP64 sums over a member's leaves of V * U (8 doubles, host). */
 icarus_status icarus_conservation_sums(icarus_ctx *ctx, int member, double *out8);
 
+/* Same result as icarus_conservation_sums, for callers that may not allocate
+ * device memory while they run (a host framework that hands the whole GPU to
+ * its own pool at start-up, a service that must never stall on an
+ * allocation).  This call allocates nothing: its scratch is a fixed array of
+ * the library's own device memory (room for 16384 leaves per member, 1 MiB),
+ * held on every GPU that loads the library until the process exits.  The
+ * paper has no counterpart; it is a service of this library.
+ *   member   member whose leaves are summed; out8: 8 doubles, host.
+ *   errors   ICARUS_ERR_CAPACITY (and a message on stderr) if the member has
+ *            more than 16384 leaves; ICARUS_ERR_ARG on bad arguments;
+ *            ICARUS_ERR_CUDA if a CUDA call fails.
+ * The first call on a device looks up the array's address (with that device
+ * current) and caches it: make that call before any stream capture.  All calls
+ * share the one array; calls that overlap on the GPU race.  Synchronises. */
+icarus_status icarus_conservation_sums_static(icarus_ctx *ctx, int member, double *out8);
+
 /* Current CFL time step of every member (host, n_members doubles). */
 icarus_status icarus_get_dt(icarus_ctx *ctx, double *dt_out);
 

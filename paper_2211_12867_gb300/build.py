@@ -18,7 +18,7 @@ BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libicarus.so")
 INCLUDE = os.path.join(os.path.dirname(HERE), "include")
 
-SOURCES = ["api.cu", "k_stage.cu", "k_ghost.cu", "k_amr.cu", "k_mlp.cu"]
+SOURCES = ["api.cu", "k_stage.cu", "k_ghost.cu", "k_amr.cu", "k_mlp.cu", "k_sums_static.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2",
          "--expt-relaxed-constexpr"]

@@ -1356,3 +1356,17 @@ icarus_status icarus_profile_read(icarus_ctx *c, double *ms, int *count, int nki
 }
 
 }  // extern "C"
+
+// Read-only view of one member's leaves for kernels that live outside this
+// file (no state is changed).
+int ctx_member_view(icarus_ctx *c, int member, KParams *kp, const void **U, int *precision, int *slot0, int *nleaves,
+                    cudaStream_t *stream) {
+  if (!c || member < 0 || member >= c->d.n_members) return -1;
+  *kp = c->kp;
+  *U = c->U;
+  *precision = c->prec;
+  *slot0 = c->mem_off[member];
+  *nleaves = (int)c->mem[member].leaves.size();
+  *stream = c->stream;
+  return 0;
+}

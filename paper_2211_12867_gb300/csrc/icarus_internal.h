@@ -146,3 +146,7 @@ void sums_launch(const KParams &kp, const void *U, int precision, int slot0, int
                  cudaStream_t s);
 void vbg_launch(const KParams &kp, const void *U, int precision, int member, int slot0, int nslots, double *vbg,
                 cudaStream_t s);
+
+struct icarus_ctx;
+int ctx_member_view(icarus_ctx *c, int member, KParams *kp, const void **U, int *precision, int *slot0,
+                    int *nleaves, cudaStream_t *stream);

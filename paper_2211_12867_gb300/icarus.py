@@ -303,3 +303,15 @@ class Icarus:
 
 PROFILE_KINDS = ["dt_begin", "ghost_neighbour", "ghost_physical", "stage_predictor", "stage_corrector",
                  "reflux", "dt_finalize"]
+
+
+def conservation_sums_static(g, member=0):
+    """Sums of V * U over a member's leaves through the entry point that
+    allocates nothing (its scratch is a fixed array inside the library)."""
+    lib = g.lib
+    f = lib.icarus_conservation_sums_static
+    f.restype = C.c_int
+    f.argtypes = [C.c_void_p, C.c_int, C.POINTER(C.c_double)]
+    out = np.zeros(8)
+    _chk("icarus_conservation_sums_static", f(g.ctx, member, _dp(out)))
+    return out
