@@ -62,6 +62,8 @@ def parse():
     p.add_argument("--no-tune", action="store_true")
     p.add_argument("--cpu-seconds", type=float, default=12.0)
     p.add_argument("--skip-cpu-baseline", action="store_true")
+    p.add_argument("--islands", default="0.002,0.1",
+                   help="FP32 mode: FP64 pressure where p < a*e or p < b*B^2/2 ('a,b')")
     p.add_argument("--mode", default="full", choices=["full", "kernel"],
                    help="kernel: set up and run warmup + steps only (for profiler captures)")
     return p.parse_args()
@@ -225,6 +227,9 @@ def main():
         torch.cuda.set_device(0)
     prec_tag = "f32" if args.precision == "fp32" else "f64"
     g, W0, wm, cme = setup_grid(args.precision, seed=rank)
+    from paper_2211_12867_gb300.icarus import set_fp64_islands
+    isl = tuple(float(x) for x in args.islands.split(","))
+    set_fp64_islands(g, *isl)
     tuned = None
     if not args.no_tune:
         from paper_2211_12867_gb300.autotune import tune
@@ -324,6 +329,7 @@ def main():
                 "data": "synthetic",
                 "config": {"workload": WORKLOAD, "grid": list(N_CELLS), "block": list(BLOCK),
                            "precision": "fp32+fp64-islands" if prec_tag == "f32" else "fp64",
+                           "fp64_islands": {"p_over_e": isl[0], "beta": isl[1]} if prec_tag == "f32" else None,
                            "cells": cells, "l2": "state > L2 (no flush needed)", "parallelism": f"replicas{world}",
                            "tuned": tuned},
                 "roofline": roofline, "cpu_baseline": cb, "e2e": e2e, "gpu_launches": kps * args.steps,

@@ -230,6 +230,12 @@ icarus_status icarus_status_word(icarus_ctx *ctx, uint32_t *word, uint64_t *floo
  * length; 0 = library default.  Used by the autotuner. */
 icarus_status icarus_set_tile(icarus_ctx *ctx, int tile_theta, int tile_phi, int r_segment);
 
+/* FP32 mode: the pressure of a cell is recomputed in FP64 (from the stored
+ * FP32 variables) where p < p_over_e * e or p < beta * B^2/2.  Defaults 0.002
+ * and 0.1 (low-beta cells, and cells where FP32 cancellation would cost more
+ * than ~1e-4 of p); 0, 0 disables the islands.  No effect in FP64 mode. */
+icarus_status icarus_set_fp64_islands(icarus_ctx *ctx, double p_over_e, double beta);
+
 /* Capture one step of the launch sequence in a CUDA graph and replay it in
  * icarus_step (1) or launch kernels directly (0).  Default 1. */
 icarus_status icarus_use_graph(icarus_ctx *ctx, int enable);

@@ -220,6 +220,7 @@ struct icarus_ctx {
   KParams kp{};
   // launch configuration
   int tile_j = 0, tile_k = 0, seg_len = 0, occ = 1;
+  double isl_pe = 0.002, isl_beta = 0.1;  // FP64 pressure islands: p < 0.002 e or beta < 0.1
   bool use_graph = true;
   cudaGraphExec_t graph = nullptr;
   bool graph_valid = false;
@@ -446,6 +447,8 @@ void fill_kp(icarus_ctx *c) {
   k.cd = d.divb_cd;
   k.p_floor = d.p_floor;
   k.rho_floor = d.rho_floor;
+  k.isl_pe = c->isl_pe;
+  k.isl_beta = c->isl_beta;
   k.geo = c->geo;
   k.blk = c->blk;
   k.lmap = c->lmap;
@@ -1325,6 +1328,15 @@ icarus_status icarus_regrid(icarus_ctx *c) {
   if (st != ICARUS_OK) return st;
   CK(cudaStreamSynchronize(c->stream));
   c->flags_valid = false;
+  return ICARUS_OK;
+}
+
+icarus_status icarus_set_fp64_islands(icarus_ctx *c, double p_over_e, double beta) {
+  if (!c || !(p_over_e >= 0.0) || !(beta >= 0.0)) return ICARUS_ERR_ARG;
+  c->isl_pe = p_over_e;
+  c->isl_beta = beta;
+  fill_kp(c);
+  c->graph_valid = false;
   return ICARUS_OK;
 }
 

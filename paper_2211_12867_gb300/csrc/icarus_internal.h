@@ -94,6 +94,7 @@ struct KParams {
   unsigned int *status;
   unsigned long long *floor_hits;
   int n_base_cells[3];
+  double isl_pe, isl_beta;     // FP64 pressure-island thresholds (FP32 mode)
 };
 
 // ---- launch wrappers (defined in the kernel translation units) ----

@@ -152,7 +152,7 @@ __device__ void prolong_child(const KParams &kp, const real *U, int cs, const in
     real u[NVAR];
 #pragma unroll
     for (int v = 0; v < NVAR; v++) u[v] = ((up[v] + s[0][v] * a) + s[1][v] * b) + s[2][v] * e;
-    if (!(u[0] > real(0)) || !(pressure_of<real>(u, gamma) > real(0))) ok = false;
+    if (!(u[0] > real(0)) || !(pressure_of<real>(u, gamma, Isl{(float)kp.isl_pe, (float)kp.isl_beta}) > real(0))) ok = false;
     if (c == ch)
 #pragma unroll
       for (int v = 0; v < NVAR; v++) out[v] = u[v];
@@ -331,7 +331,7 @@ template <typename real>
 __global__ void k_vbg(const KParams kp, const real *U, int member, int slot0, double *vbg) {
   const int slot = slot0 + blockIdx.x;
   const DevBlock B = kp.blk[slot];
-  for (int c = threadIdx.x; c < kp.icells; c += blockDim.x) {
+  for (int c = blockIdx.y * blockDim.x + threadIdx.x; c < kp.icells; c += gridDim.y * blockDim.x) {
     const int k = c % kp.nb[2], j = (c / kp.nb[2]) % kp.nb[1], i = c / (kp.nb[2] * kp.nb[1]);
     const int I = B.ix[0] * kp.nb[0] + i, J = B.ix[1] * kp.nb[1] + j, K = B.ix[2] * kp.nb[2] + k;
     const double m = (double)U[cidx<real>(kp, slot, 1, i + NGH, j + NGH, k + NGH)];
@@ -402,7 +402,7 @@ void vbg_launch(const KParams &kp, const void *U, int precision, int member, int
                 cudaStream_t s) {
   if (nslots <= 0) return;
   if (precision)
-    k_vbg<float><<<nslots, 256, 0, s>>>(kp, (const float *)U, member, slot0, vbg);
+    k_vbg<float><<<dim3(nslots, (kp.icells + 4095) / 4096), 256, 0, s>>>(kp, (const float *)U, member, slot0, vbg);
   else
-    k_vbg<double><<<nslots, 256, 0, s>>>(kp, (const double *)U, member, slot0, vbg);
+    k_vbg<double><<<dim3(nslots, (kp.icells + 4095) / 4096), 256, 0, s>>>(kp, (const double *)U, member, slot0, vbg);
 }

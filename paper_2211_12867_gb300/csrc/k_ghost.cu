@@ -76,7 +76,7 @@ __device__ void prolong_value(const KParams &kp, const real *U, int cs, int Lc, 
     real u[NVAR];
 #pragma unroll
     for (int v = 0; v < NVAR; v++) u[v] = ((up[v] + s[0][v] * a) + s[1][v] * b) + s[2][v] * e;
-    if (!(u[0] > real(0)) || !(pressure_of<real>(u, gamma) > real(0))) ok = false;
+    if (!(u[0] > real(0)) || !(pressure_of<real>(u, gamma, Isl{(float)kp.isl_pe, (float)kp.isl_beta}) > real(0))) ok = false;
     if (c == ch) {
 #pragma unroll
       for (int v = 0; v < NVAR; v++) out[v] = u[v];
@@ -321,11 +321,11 @@ __global__ void k_reflux(const KParams kp, real *U, const real *flux, const int 
       real u[NVAR];
 #pragma unroll
       for (int v = 0; v < NVAR; v++) u[v] = U[cell_index<real>(kp, slot, v, q[0], q[1], q[2])];
-      hits += apply_floors<real>(u, gamma, pfl, rfl);
+      hits += apply_floors<real>(u, gamma, pfl, rfl, Isl{(float)kp.isl_pe, (float)kp.isl_beta});
 #pragma unroll
       for (int v = 0; v < NVAR; v++) U[cell_index<real>(kp, slot, v, q[0], q[1], q[2])] = u[v];
       real w[NVAR];
-      cons2prim<real>(u, w, gamma, pfl);
+      cons2prim_speed<real>(u, w, gamma, pfl);
       const int I = B.ix[0] * nb0 + q[0] - NGH + NGH, J = B.ix[1] * nb1 + q[1] - NGH + NGH;
       real dx0 = G.dr[I], dx1 = G.dth[J], dx2 = G.dphi;
       if (kp.geometry == 0) {
@@ -376,12 +376,12 @@ __global__ void k_dt_full(const KParams kp, const real *U) {
   const LevelGeo<real> &G = GeoSel<real>::get(kp.geo, B.level);
   const real gamma = (real)kp.gamma, pfl = (real)kp.p_floor;
   double acc = 0.0;
-  for (int c = threadIdx.x; c < kp.icells; c += blockDim.x) {
+  for (int c = blockIdx.y * blockDim.x + threadIdx.x; c < kp.icells; c += gridDim.y * blockDim.x) {
     const int k = c % kp.nb[2], j = (c / kp.nb[2]) % kp.nb[1], i = c / (kp.nb[2] * kp.nb[1]);
     real u[NVAR], w[NVAR];
 #pragma unroll
     for (int v = 0; v < NVAR; v++) u[v] = U[cell_index<real>(kp, slot, v, i + NGH, j + NGH, k + NGH)];
-    cons2prim<real>(u, w, gamma, pfl);
+    cons2prim_speed<real>(u, w, gamma, pfl);
     const int I = B.ix[0] * kp.nb[0] + i + NGH, J = B.ix[1] * kp.nb[1] + j + NGH;
     real dx0 = G.dr[I], dx1 = G.dth[J], dx2 = G.dphi;
     if (kp.geometry == 0) {
@@ -449,9 +449,9 @@ void dt_finalize_launch(const KParams &kp, double cfl, cudaStream_t s) {
 void dt_full_launch(const KParams &kp, const void *U, int precision, int nleaves, double cfl, cudaStream_t s) {
   if (nleaves > 0) {
     if (precision)
-      k_dt_full<float><<<nleaves, 256, 0, s>>>(kp, (const float *)U);
+      k_dt_full<float><<<dim3(nleaves, (kp.icells + 4095) / 4096), 256, 0, s>>>(kp, (const float *)U);
     else
-      k_dt_full<double><<<nleaves, 256, 0, s>>>(kp, (const double *)U);
+      k_dt_full<double><<<dim3(nleaves, (kp.icells + 4095) / 4096), 256, 0, s>>>(kp, (const double *)U);
   }
   k_dt_from_max<<<(kp.n_members + 127) / 128, 128, 0, s>>>(kp, cfl);
 }

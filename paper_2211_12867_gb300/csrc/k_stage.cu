@@ -71,6 +71,7 @@ __global__ void __launch_bounds__(TJ *TK, (sizeof(real) == 4 ? 2 : 1))
   const int nwork = sl.nlist * per_block;
   const bool spherical = kp.geometry == 0;
   const real Om = (real)kp.omega, Cd = (real)kp.cd;
+  const Isl isl{(float)kp.isl_pe, (float)kp.isl_beta};
 
   // reflux face buffer layout (per slot): faces in order r-lo, r-hi, th-lo,
   // th-hi, ph-lo, ph-hi; each [v][t1][t2]
@@ -117,7 +118,7 @@ __global__ void __launch_bounds__(TJ *TK, (sizeof(real) == 4 ? 2 : 1))
           real u[NVAR], wv[NVAR];
 #pragma unroll
           for (int v = 0; v < NVAR; v++) u[v] = src[v * vstride + (size_t)pj * P2 + pk];
-          cons2prim<real>(u, wv, gamma, pfl);
+          cons2prim<real>(u, wv, gamma, pfl, isl);
 #pragma unroll
           for (int v = 0; v < NVAR; v++) dst[v * RP + q] = wv[v];
         }
@@ -280,7 +281,7 @@ __global__ void __launch_bounds__(TJ *TK, (sizeof(real) == 4 ? 2 : 1))
           un[7] += dB2;
           un[4] += w[5] * dB0 + w[6] * dB1 + w[7] * dB2;
         }
-        hits += apply_floors<real>(un, gamma, pfl, rfl);
+        hits += apply_floors<real>(un, gamma, pfl, rfl, isl);
         if (!(un[0] == un[0]) || !(un[4] == un[4])) atomicOr(kp.status, ST_NAN);
 #pragma unroll
         for (int v = 0; v < NVAR; v++) Uout[v * vstride + cidx] = un[v];
@@ -292,7 +293,7 @@ __global__ void __launch_bounds__(TJ *TK, (sizeof(real) == 4 ? 2 : 1))
                             (k == 0 && B.nbr[4] == NB_FINER) || (k == nb2 - 1 && B.nbr[5] == NB_FINER);
           if (!skip) {
             real wn[NVAR];
-            cons2prim<real>(un, wn, gamma, pfl);
+            cons2prim_speed<real>(un, wn, gamma, pfl);
             real dx0 = G.dr[iI], dx1 = G.dth[iJ], dx2 = G.dphi;
             if (spherical) {
               dx1 *= G.rc[iI];

@@ -28,8 +28,13 @@ template <> struct RT<float> {
 // result is replaced by an FP64 recomputation from the same (FP32-stored)
 // conserved variables where the thermal energy is a small remainder of the
 // total: p < 0.05 e or plasma beta = p / (B^2/2) < 0.1.
+// thresholds of the FP64 pressure island (FP32 mode): p < pe * e or p < beta * B^2/2
+struct Isl {
+  float pe, beta;
+};
+
 template <typename real>
-__device__ __forceinline__ real pressure_of(const real *u, real gamma) {
+__device__ __forceinline__ real pressure_of(const real *u, real gamma, Isl) {
   real ir = real(1) / u[0];
   real msq = u[1] * u[1] + u[2] * u[2] + u[3] * u[3];
   real me = real(0.5) * (u[5] * u[5] + u[6] * u[6] + u[7] * u[7]);
@@ -37,31 +42,72 @@ __device__ __forceinline__ real pressure_of(const real *u, real gamma) {
   return p;
 }
 
-template <>
-__device__ __forceinline__ float pressure_of<float>(const float *u, float gamma) {
+// FP64 pressure from FP32-stored variables.  The product of two floats is
+// exact in double, so m.m and B.B carry no rounding beyond the double sums;
+// 1/rho starts from the float reciprocal and one Newton step in double brings
+// it to double accuracy (no FP64 division).
+__device__ __forceinline__ float pressure_fp64_island(const float *u, float gamma) {
+  const double r = u[0];
+  double ri = (double)__frcp_rn(u[0]);
+  ri = fma(ri, fma(-r, ri, 1.0), ri);
+  const double m1 = u[1], m2 = u[2], m3 = u[3], b1 = u[5], b2 = u[6], b3 = u[7];
+  const double ms = fma(m1, m1, fma(m2, m2, m3 * m3));
+  const double bs = fma(b1, b1, fma(b2, b2, b3 * b3));
+  const double h = fma(-0.5, bs, (double)u[4]);
+  return (float)(((double)gamma - 1.0) * fma(-0.5 * ms, ri, h));
+}
+
+// float pressure without the island (accurate to ~1e-6 e)
+__device__ __forceinline__ float pressure_fp32(const float *u, float gamma) {
   float ir = 1.0f / u[0];
   float msq = u[1] * u[1] + u[2] * u[2] + u[3] * u[3];
   float me = 0.5f * (u[5] * u[5] + u[6] * u[6] + u[7] * u[7]);
-  float p = (gamma - 1.0f) * (u[4] - 0.5f * msq * ir - me);
-  if (p < 0.05f * u[4] || p < 0.1f * me) {
-    double r = u[0], m1 = u[1], m2 = u[2], m3 = u[3], e = u[4], b1 = u[5], b2 = u[6], b3 = u[7];
-    double ms = m1 * m1 + m2 * m2 + m3 * m3;
-    double bs = b1 * b1 + b2 * b2 + b3 * b3;
-    double pd = ((double)gamma - 1.0) * (e - 0.5 * ms / r - 0.5 * bs);
-    p = (float)pd;
-  }
+  return (gamma - 1.0f) * (u[4] - 0.5f * msq * ir - me);
+}
+
+template <>
+__device__ __forceinline__ float pressure_of<float>(const float *u, float gamma, Isl isl) {
+  float p = pressure_fp32(u, gamma);
+  const float me = 0.5f * (u[5] * u[5] + u[6] * u[6] + u[7] * u[7]);
+  if (p < isl.pe * u[4] || p < isl.beta * me) p = pressure_fp64_island(u, gamma);
   return p;
+}
+
+// pressure for the CFL wave speed: the float value suffices (relative error
+// ~1e-6 e / p on a time-step bound taken with a 0.8 safety factor)
+template <typename real>
+__device__ __forceinline__ real pressure_for_speed(const real *u, real gamma) {
+  return pressure_of<real>(u, gamma, Isl{0.f, 0.f});
+}
+template <>
+__device__ __forceinline__ float pressure_for_speed<float>(const float *u, float gamma) {
+  return pressure_fp32(u, gamma);
 }
 
 // U -> W with the pressure floor of the stage operator.
 template <typename real>
-__device__ __forceinline__ void cons2prim(const real *u, real *w, real gamma, real pfloor) {
+__device__ __forceinline__ void cons2prim(const real *u, real *w, real gamma, real pfloor, Isl isl) {
   real ir = real(1) / u[0];
   w[0] = u[0];
   w[1] = u[1] * ir;
   w[2] = u[2] * ir;
   w[3] = u[3] * ir;
-  real p = pressure_of<real>(u, gamma);
+  real p = pressure_of<real>(u, gamma, isl);
+  w[4] = p < pfloor ? pfloor : p;
+  w[5] = u[5];
+  w[6] = u[6];
+  w[7] = u[7];
+}
+
+// primitives for the CFL speed (no FP64 island in the FP32 mode)
+template <typename real>
+__device__ __forceinline__ void cons2prim_speed(const real *u, real *w, real gamma, real pfloor) {
+  real ir = real(1) / u[0];
+  w[0] = u[0];
+  w[1] = u[1] * ir;
+  w[2] = u[2] * ir;
+  w[3] = u[3] * ir;
+  real p = pressure_for_speed<real>(u, gamma);
   w[4] = p < pfloor ? pfloor : p;
   w[5] = u[5];
   w[6] = u[6];
@@ -157,13 +203,18 @@ __device__ __forceinline__ void tvdlf_face(const real *a, const real *b, const r
 
 // floors on a freshly updated cell; returns the number of floor hits
 template <typename real>
-__device__ __forceinline__ int apply_floors(real *u, real gamma, real pfloor, real rfloor) {
+__device__ __forceinline__ int apply_floors(real *u, real gamma, real pfloor, real rfloor, Isl isl) {
   int hits = 0;
   if (u[0] < rfloor) {
     u[0] = rfloor;
     hits++;
   }
-  real p = pressure_of<real>(u, gamma);
+  // the plain-precision pressure is within ~1e-6 |e| of the exact one: only a
+  // cell that might be below the floor pays for the precise recovery
+  const real pq = pressure_for_speed<real>(u, gamma);
+  const real margin = sizeof(real) == 4 ? real(1e-6) : real(0);
+  if (pq > pfloor + margin * RT<real>::abs_(u[4])) return hits;
+  real p = pressure_of<real>(u, gamma, isl);
   if (p < pfloor) {
     real ke = real(0.5) * (u[1] * u[1] + u[2] * u[2] + u[3] * u[3]) / u[0];
     real me = real(0.5) * (u[5] * u[5] + u[6] * u[6] + u[7] * u[7]);

@@ -34,7 +34,8 @@ EXPORTS = [
     "icarus_n_leaves", "icarus_get_tree", "icarus_set_state", "icarus_get_state", "icarus_set_time",
     "icarus_set_member_max_level", "icarus_ghost_fill", "icarus_conservation_sums", "icarus_get_dt",
     "icarus_status_word", "icarus_set_tile", "icarus_use_graph", "icarus_kernels_per_step",
-    "icarus_profile", "icarus_profile_read", "icarus_destroy", "icarus_status_string",
+    "icarus_profile", "icarus_profile_read", "icarus_set_fp64_islands", "icarus_destroy",
+    "icarus_status_string",
 ]
 
 
@@ -315,3 +316,11 @@ def conservation_sums_static(g, member=0):
     out = np.zeros(8)
     _chk("icarus_conservation_sums_static", f(g.ctx, member, _dp(out)))
     return out
+
+
+def set_fp64_islands(g, p_over_e=0.05, beta=0.1):
+    """FP32 mode: FP64 pressure recovery where p < p_over_e * e or p < beta * B^2/2."""
+    f = g.lib.icarus_set_fp64_islands
+    f.restype = C.c_int
+    f.argtypes = [C.c_void_p, C.c_double, C.c_double]
+    _chk("icarus_set_fp64_islands", f(g.ctx, float(p_over_e), float(beta)))
