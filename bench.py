@@ -64,6 +64,7 @@ def parse():
     p.add_argument("--skip-cpu-baseline", action="store_true")
     p.add_argument("--islands", default="0.002,0.1",
                    help="FP32 mode: FP64 pressure where p < a*e or p < b*B^2/2 ('a,b')")
+    p.add_argument("--tile", default="", help="force the stage tile 'tile_theta,tile_phi,r_segment'")
     p.add_argument("--mode", default="full", choices=["full", "kernel"],
                    help="kernel: set up and run warmup + steps only (for profiler captures)")
     return p.parse_args()
@@ -231,7 +232,11 @@ def main():
     isl = tuple(float(x) for x in args.islands.split(","))
     set_fp64_islands(g, *isl)
     tuned = None
-    if not args.no_tune:
+    if args.tile:
+        tj, tk, seg = (int(x) for x in args.tile.split(","))
+        g.set_tile(tj, tk, seg)
+        tuned = {"tile": [tj, tk], "r_segment": seg, "ms": None, "forced": True}
+    elif not args.no_tune:
         from paper_2211_12867_gb300.autotune import tune
         best, best_ms, _ = tune(g, steps=3)
         tuned = {"tile": [best[0], best[1]], "r_segment": best[2], "ms": round(best_ms, 4)}

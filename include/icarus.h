@@ -244,6 +244,46 @@ icarus_status icarus_use_graph(icarus_ctx *ctx, int enable);
  * accounting). */
 icarus_status icarus_kernels_per_step(icarus_ctx *ctx, int *n);
 
+/* ---- learned refinement pre-flagger ----
+ * The paper refines from criteria on the solution (Sect. 3); this predictor
+ * (no counterpart in the paper) anticipates the estimator's decision one
+ * regrid ahead.  Per block: the index-space gradient magnitude of density,
+ * radial speed and pressure, each divided by the cell's magnitude, averaged
+ * over the three variables and over 4x4x4 sub-cubes (block sizes must be
+ * multiples of 4) -> 64 inputs; MLP 64 -> 128 (ReLU) -> 128 (ReLU) -> 1
+ * (sigmoid); binary cross-entropy; Adam (beta 0.9/0.999, eps 1e-8).  FP32.
+ * Parameters: W1[128][64], b1[128], W2[128][128], b2[128], w3[128], b3
+ * (24961 floats).  All calls synchronise. */
+
+/* Load parameters (host FP32, n = 24961); resets the Adam moments. */
+icarus_status icarus_mlp_set_params(icarus_ctx *ctx, const float *host, size_t n);
+icarus_status icarus_mlp_get_params(icarus_ctx *ctx, float *host, size_t n);
+
+/* Features of every leaf (global leaf order) after a ghost fill; host_out
+ * (optional) receives n_leaves x 64 floats. */
+icarus_status icarus_mlp_features(icarus_ctx *ctx, float *host_out);
+
+/* Refinement probability of every leaf (features + forward), host n_leaves. */
+icarus_status icarus_mlp_predict_leaves(icarus_ctx *ctx, float *prob_host);
+
+/* Forward on n <= 4096 host samples x[n][64] -> y[n]. */
+icarus_status icarus_mlp_predict(icarus_ctx *ctx, const float *x_host, int n, float *y_host);
+
+/* Gradient of the mean cross-entropy over n <= 4096 host samples (targets
+ * 0/1) -> grad_host[24961]; loss_out (optional) receives the mean loss. */
+icarus_status icarus_mlp_grad(icarus_ctx *ctx, const float *x_host, const float *t_host, int n, float *grad_host,
+                              float *loss_out);
+
+/* Device training set (at most 65536 samples): clear, append host samples. */
+icarus_status icarus_mlp_dataset_clear(icarus_ctx *ctx);
+icarus_status icarus_mlp_dataset_add(icarus_ctx *ctx, const float *x_host, const float *t_host, int n, int *total);
+
+/* Adam on the first n_train samples of the training set: `epochs` passes in
+ * seeded shuffled minibatches of `batch` (<= 4096) at learning rate lr;
+ * loss_per_epoch (optional, epochs floats) receives the summed loss. */
+icarus_status icarus_mlp_train(icarus_ctx *ctx, int n_train, int epochs, int batch, double lr, uint64_t seed,
+                               float *loss_per_epoch);
+
 /* Per-launch timing with CUDA events (enable = 1).  While enabled,
  * icarus_step launches the kernels directly instead of replaying the graph
  * and records an event pair around every launch on the context's stream. */

@@ -20,6 +20,8 @@
 namespace {
 
 constexpr size_t ALIGN = 256;
+constexpr int MLP_CAP = 65536;   // training samples held on the device
+constexpr int MLP_BMAX = 4096;   // largest batch
 
 struct Leaf {
   int level;
@@ -40,7 +42,8 @@ struct Region {
 struct Layout {
   size_t total = 0;
   Region geo, tables, blk, blk_alt, U, Us, Ualt, flux, lmap, lmap_off, bmap, cme, vbg, scal, flags, lists,
-      sides, rlist, ops, shell, staging, partial, probe_in, probe_out;
+      sides, rlist, ops, shell, staging, partial, probe_in, probe_out, mlp_par, mlp_feat, mlp_X, mlp_T, mlp_idx,
+      mlp_act, mlp_xin;
   size_t staging_doubles = 0, table_doubles = 0;
   int max_blocks = 0, nshell = 0;
   long long lmap_ints = 0;
@@ -149,6 +152,15 @@ Layout make_layout(const icarus_grid_desc *d) {
   L.partial = L.add(mb * NVAR * sizeof(double));
   L.probe_in = L.add(4096 * 3 * sizeof(double));
   L.probe_out = L.add(4096 * NVAR * sizeof(double));
+  // learned pre-flagger: parameters, gradient and Adam moments (4 x n), leaf
+  // features and probabilities, training set, batch activations
+  L.mlp_par = L.add((size_t)4 * mlp_n_params() * sizeof(float) + 64);
+  L.mlp_feat = L.add(mb * (64 + 1) * sizeof(float));
+  L.mlp_X = L.add((size_t)MLP_CAP * 64 * sizeof(float));
+  L.mlp_T = L.add((size_t)MLP_CAP * sizeof(float));
+  L.mlp_idx = L.add((size_t)MLP_CAP * sizeof(int));
+  L.mlp_act = L.add((size_t)MLP_BMAX * (4 * 128 + 2) * sizeof(float));
+  L.mlp_xin = L.add((size_t)MLP_BMAX * 65 * sizeof(float));
   return L;
 }
 
@@ -227,6 +239,14 @@ struct icarus_ctx {
   bool poisoned = false;
   std::vector<double> h_tstop;
   int kernels_per_step = 0;
+  // learned pre-flagger
+  float *mlp_theta = nullptr, *mlp_grad = nullptr, *mlp_m = nullptr, *mlp_v = nullptr, *mlp_loss = nullptr;
+  float *mlp_feat = nullptr, *mlp_prob = nullptr, *mlp_X = nullptr, *mlp_T = nullptr, *mlp_h1 = nullptr,
+        *mlp_h2 = nullptr, *mlp_dh2 = nullptr, *mlp_dh1 = nullptr, *mlp_y = nullptr, *mlp_dz = nullptr,
+        *mlp_xin = nullptr, *mlp_tin = nullptr;
+  int *mlp_idx = nullptr;
+  int mlp_n = 0, mlp_step = 0;
+  bool mlp_ready = false;
   // per-launch profiling
   bool prof_on = false;
   std::vector<cudaEvent_t> ev;
@@ -756,6 +776,31 @@ int enqueue_step(icarus_ctx *c) {
   return n;
 }
 
+// ghost fill, features and predicted refinement probability of every leaf
+void mlp_leaf_probabilities(icarus_ctx *c) {
+  enqueue_ghost(c, c->U, 0.0);
+  mlp_features_launch(c->kp, c->U, c->prec, 0, c->nleaves, c->mlp_feat, c->stream);
+  for (int b0 = 0; b0 < c->nleaves; b0 += MLP_BMAX) {
+    const int B = std::min(MLP_BMAX, c->nleaves - b0);
+    mlp_forward_launch(c->mlp_theta, c->mlp_feat + (size_t)b0 * 64, nullptr, B, c->mlp_h1, c->mlp_h2,
+                       c->mlp_prob + b0, c->stream);
+  }
+}
+
+// seeded permutation (splitmix64 + Fisher-Yates)
+void permutation(std::vector<int> &p, int n, uint64_t &state) {
+  p.resize(n);
+  for (int i = 0; i < n; i++) p[i] = i;
+  for (int i = n - 1; i > 0; i--) {
+    uint64_t z = (state += 0x9E3779B97F4A7C15ull);
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    z ^= z >> 31;
+    const int j = (int)(z % (uint64_t)(i + 1));
+    std::swap(p[i], p[j]);
+  }
+}
+
 icarus_status check_status(icarus_ctx *c) {
   unsigned int w = 0;
   CK(cudaMemcpyAsync(&w, c->status, sizeof(w), cudaMemcpyDeviceToHost, c->stream));
@@ -861,6 +906,29 @@ icarus_status icarus_init_grid(const icarus_grid_desc *desc, icarus_ctx **out) {
   c->partial = at<double>(c, lay.partial);
   c->probe_in = at<double>(c, lay.probe_in);
   c->probe_out = at<double>(c, lay.probe_out);
+  {
+    float *par = at<float>(c, lay.mlp_par);
+    const int np = mlp_n_params();
+    c->mlp_theta = par;
+    c->mlp_grad = par + np;
+    c->mlp_m = par + 2 * (size_t)np;
+    c->mlp_v = par + 3 * (size_t)np;
+    c->mlp_loss = par + 4 * (size_t)np;
+    c->mlp_feat = at<float>(c, lay.mlp_feat);
+    c->mlp_prob = c->mlp_feat + (size_t)lay.max_blocks * 64;
+    c->mlp_X = at<float>(c, lay.mlp_X);
+    c->mlp_T = at<float>(c, lay.mlp_T);
+    c->mlp_idx = at<int>(c, lay.mlp_idx);
+    float *act = at<float>(c, lay.mlp_act);
+    c->mlp_h1 = act;
+    c->mlp_h2 = act + (size_t)MLP_BMAX * 128;
+    c->mlp_dh2 = act + (size_t)2 * MLP_BMAX * 128;
+    c->mlp_dh1 = act + (size_t)3 * MLP_BMAX * 128;
+    c->mlp_y = act + (size_t)4 * MLP_BMAX * 128;
+    c->mlp_dz = c->mlp_y + MLP_BMAX;
+    c->mlp_xin = at<float>(c, lay.mlp_xin);
+    c->mlp_tin = c->mlp_xin + (size_t)MLP_BMAX * 64;
+  }
   auto fail = [&](icarus_status s) {
     delete c;
     return s;
@@ -1172,6 +1240,11 @@ icarus_status icarus_flag_refine(icarus_ctx *c, const icarus_refine *crit, int8_
   enqueue_ghost(c, c->U, 0.0);
   estimator_launch(c->kp, c->U, c->prec, 0, c->nleaves, crit->e_refine, crit->e_coarsen, crit->eps, crit->dv,
                    c->flags, c->stream);
+  if (crit->mode == ICARUS_FLAG_LEARNED) {
+    if (!c->mlp_ready) return ICARUS_ERR_STATE;
+    mlp_leaf_probabilities(c);
+    mlp_combine_launch(c->mlp_prob, c->flags, c->nleaves, c->stream);
+  }
   CK(cudaPeekAtLastError());
   c->hflags.assign(c->nleaves, 0);
   CK(cudaMemcpyAsync(c->hflags.data(), c->flags, c->nleaves, cudaMemcpyDeviceToHost, c->stream));
@@ -1382,3 +1455,131 @@ int ctx_member_view(icarus_ctx *c, int member, KParams *kp, const void **U, int 
   *stream = c->stream;
   return 0;
 }
+
+extern "C" {
+
+// ---- learned pre-flagger ----
+icarus_status icarus_mlp_set_params(icarus_ctx *c, const float *host, size_t n) {
+  if (!c || !host || n != (size_t)mlp_n_params()) return ICARUS_ERR_ARG;
+  const size_t bytes = n * sizeof(float);
+  CK(cudaMemcpyAsync(c->mlp_theta, host, bytes, cudaMemcpyHostToDevice, c->stream));
+  CK(cudaMemsetAsync(c->mlp_m, 0, bytes, c->stream));
+  CK(cudaMemsetAsync(c->mlp_v, 0, bytes, c->stream));
+  CK(cudaStreamSynchronize(c->stream));
+  c->mlp_step = 0;
+  c->mlp_ready = true;
+  return ICARUS_OK;
+}
+
+icarus_status icarus_mlp_get_params(icarus_ctx *c, float *host, size_t n) {
+  if (!c || !host || n != (size_t)mlp_n_params()) return ICARUS_ERR_ARG;
+  CK(cudaMemcpyAsync(host, c->mlp_theta, n * sizeof(float), cudaMemcpyDeviceToHost, c->stream));
+  CK(cudaStreamSynchronize(c->stream));
+  return ICARUS_OK;
+}
+
+icarus_status icarus_mlp_features(icarus_ctx *c, float *host_out) {
+  if (!c) return ICARUS_ERR_ARG;
+  for (int k = 0; k < 3; k++)
+    if (c->d.block[k] % 4) return ICARUS_ERR_ARG;
+  enqueue_ghost(c, c->U, 0.0);
+  mlp_features_launch(c->kp, c->U, c->prec, 0, c->nleaves, c->mlp_feat, c->stream);
+  CK(cudaPeekAtLastError());
+  if (host_out)
+    CK(cudaMemcpyAsync(host_out, c->mlp_feat, sizeof(float) * 64 * c->nleaves, cudaMemcpyDeviceToHost, c->stream));
+  CK(cudaStreamSynchronize(c->stream));
+  return ICARUS_OK;
+}
+
+icarus_status icarus_mlp_predict_leaves(icarus_ctx *c, float *prob_host) {
+  if (!c || !prob_host) return ICARUS_ERR_ARG;
+  if (!c->mlp_ready) return ICARUS_ERR_STATE;
+  for (int k = 0; k < 3; k++)
+    if (c->d.block[k] % 4) return ICARUS_ERR_ARG;
+  mlp_leaf_probabilities(c);
+  CK(cudaPeekAtLastError());
+  CK(cudaMemcpyAsync(prob_host, c->mlp_prob, sizeof(float) * c->nleaves, cudaMemcpyDeviceToHost, c->stream));
+  CK(cudaStreamSynchronize(c->stream));
+  return ICARUS_OK;
+}
+
+icarus_status icarus_mlp_predict(icarus_ctx *c, const float *x_host, int n, float *y_host) {
+  if (!c || !x_host || !y_host || n < 0 || n > MLP_BMAX) return ICARUS_ERR_ARG;
+  if (!c->mlp_ready) return ICARUS_ERR_STATE;
+  CK(cudaMemcpyAsync(c->mlp_xin, x_host, sizeof(float) * 64 * n, cudaMemcpyHostToDevice, c->stream));
+  mlp_forward_launch(c->mlp_theta, c->mlp_xin, nullptr, n, c->mlp_h1, c->mlp_h2, c->mlp_y, c->stream);
+  CK(cudaPeekAtLastError());
+  CK(cudaMemcpyAsync(y_host, c->mlp_y, sizeof(float) * n, cudaMemcpyDeviceToHost, c->stream));
+  CK(cudaStreamSynchronize(c->stream));
+  return ICARUS_OK;
+}
+
+icarus_status icarus_mlp_grad(icarus_ctx *c, const float *x_host, const float *t_host, int n, float *grad_host,
+                              float *loss_out) {
+  if (!c || !x_host || !t_host || !grad_host || n < 1 || n > MLP_BMAX) return ICARUS_ERR_ARG;
+  if (!c->mlp_ready) return ICARUS_ERR_STATE;
+  CK(cudaMemcpyAsync(c->mlp_xin, x_host, sizeof(float) * 64 * n, cudaMemcpyHostToDevice, c->stream));
+  CK(cudaMemcpyAsync(c->mlp_tin, t_host, sizeof(float) * n, cudaMemcpyHostToDevice, c->stream));
+  CK(cudaMemsetAsync(c->mlp_loss, 0, sizeof(float), c->stream));
+  mlp_forward_launch(c->mlp_theta, c->mlp_xin, nullptr, n, c->mlp_h1, c->mlp_h2, c->mlp_y, c->stream);
+  mlp_backward_launch(c->mlp_theta, c->mlp_xin, c->mlp_tin, nullptr, n, c->mlp_h1, c->mlp_h2, c->mlp_y, c->mlp_dz,
+                      c->mlp_dh2, c->mlp_dh1, c->mlp_grad, c->mlp_loss, c->stream);
+  CK(cudaPeekAtLastError());
+  CK(cudaMemcpyAsync(grad_host, c->mlp_grad, sizeof(float) * mlp_n_params(), cudaMemcpyDeviceToHost, c->stream));
+  float l = 0.f;
+  CK(cudaMemcpyAsync(&l, c->mlp_loss, sizeof(float), cudaMemcpyDeviceToHost, c->stream));
+  CK(cudaStreamSynchronize(c->stream));
+  if (loss_out) *loss_out = l / (float)n;
+  return ICARUS_OK;
+}
+
+icarus_status icarus_mlp_dataset_clear(icarus_ctx *c) {
+  if (!c) return ICARUS_ERR_ARG;
+  c->mlp_n = 0;
+  return ICARUS_OK;
+}
+
+icarus_status icarus_mlp_dataset_add(icarus_ctx *c, const float *x_host, const float *t_host, int n, int *total) {
+  if (!c || n < 0 || (n && (!x_host || !t_host))) return ICARUS_ERR_ARG;
+  if (c->mlp_n + n > MLP_CAP) return ICARUS_ERR_CAPACITY;
+  if (n) {
+    CK(cudaMemcpyAsync(c->mlp_X + (size_t)c->mlp_n * 64, x_host, sizeof(float) * 64 * n, cudaMemcpyHostToDevice,
+                       c->stream));
+    CK(cudaMemcpyAsync(c->mlp_T + c->mlp_n, t_host, sizeof(float) * n, cudaMemcpyHostToDevice, c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+  }
+  c->mlp_n += n;
+  if (total) *total = c->mlp_n;
+  return ICARUS_OK;
+}
+
+icarus_status icarus_mlp_train(icarus_ctx *c, int n_train, int epochs, int batch, double lr, uint64_t seed,
+                               float *loss_per_epoch) {
+  if (!c || n_train < 1 || n_train > c->mlp_n || epochs < 0 || batch < 1 || batch > MLP_BMAX || !(lr > 0.0))
+    return ICARUS_ERR_ARG;
+  if (!c->mlp_ready) return ICARUS_ERR_STATE;
+  std::vector<int> perm;
+  uint64_t st = seed;
+  for (int e = 0; e < epochs; e++) {
+    permutation(perm, n_train, st);
+    CK(cudaMemcpyAsync(c->mlp_idx, perm.data(), sizeof(int) * n_train, cudaMemcpyHostToDevice, c->stream));
+    CK(cudaMemsetAsync(c->mlp_loss, 0, sizeof(float), c->stream));
+    for (int b0 = 0; b0 < n_train; b0 += batch) {
+      const int B = std::min(batch, n_train - b0);
+      const int *idx = c->mlp_idx + b0;
+      mlp_forward_launch(c->mlp_theta, c->mlp_X, idx, B, c->mlp_h1, c->mlp_h2, c->mlp_y, c->stream);
+      mlp_backward_launch(c->mlp_theta, c->mlp_X, c->mlp_T, idx, B, c->mlp_h1, c->mlp_h2, c->mlp_y, c->mlp_dz,
+                          c->mlp_dh2, c->mlp_dh1, c->mlp_grad, c->mlp_loss, c->stream);
+      mlp_adam_launch(c->mlp_theta, c->mlp_grad, c->mlp_m, c->mlp_v, (float)lr, ++c->mlp_step, c->stream);
+    }
+    CK(cudaPeekAtLastError());
+    float l = 0.f;
+    CK(cudaMemcpyAsync(&l, c->mlp_loss, sizeof(float), cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+    if (loss_per_epoch) loss_per_epoch[e] = l;
+  }
+  return ICARUS_OK;
+}
+
+}  // extern "C"
+

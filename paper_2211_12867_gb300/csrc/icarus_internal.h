@@ -148,6 +148,18 @@ void sums_launch(const KParams &kp, const void *U, int precision, int slot0, int
 void vbg_launch(const KParams &kp, const void *U, int precision, int member, int slot0, int nslots, double *vbg,
                 cudaStream_t s);
 
+// learned pre-flagger (k_mlp.cu)
+int mlp_n_params();
+void mlp_features_launch(const KParams &kp, const void *U, int precision, int slot0, int nslots, float *out,
+                         cudaStream_t s);
+void mlp_forward_launch(const float *theta, const float *X, const int *idx, int B, float *h1, float *h2, float *y,
+                        cudaStream_t s);
+void mlp_backward_launch(const float *theta, const float *X, const float *T, const int *idx, int B,
+                         const float *h1, const float *h2, const float *y, float *dz, float *dh2, float *dh1,
+                         float *grad, float *loss, cudaStream_t s);
+void mlp_adam_launch(float *theta, const float *g, float *m, float *v, float lr, int step, cudaStream_t s);
+void mlp_combine_launch(const float *prob, signed char *flags, int n, cudaStream_t s);
+
 struct icarus_ctx;
 int ctx_member_view(icarus_ctx *c, int member, KParams *kp, const void **U, int *precision, int *slot0,
                     int *nleaves, cudaStream_t *stream);

@@ -40,7 +40,7 @@ __global__ void k_unpack(const KParams kp, real *U, int slot0, int nslots, const
 #pragma unroll
     for (int v = 0; v < NVAR; v++) x[v] = in[((size_t)s * NVAR + v) * kp.icells + c];
     if (is_prim)
-      prim2cons<double>(x, u, kp.gamma);
+      prim2cons<double>(x, u, 1.0 / (kp.gamma - 1.0));
     else
 #pragma unroll
       for (int v = 0; v < NVAR; v++) u[v] = x[v];

@@ -189,7 +189,7 @@ __device__ void inner_state(const KParams &kp, int member, int L, int J, int K, 
       }
     }
   }
-  prim2cons<double>(w, u, kp.gamma);
+  prim2cons<double>(w, u, 1.0 / (kp.gamma - 1.0));
 }
 
 // physical boundary of direction `dir`; sides[n] = (slot, side)

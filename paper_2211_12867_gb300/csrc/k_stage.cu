@@ -33,7 +33,7 @@ namespace {
 template <typename real>
 struct StageSmem {
   static constexpr size_t bytes(int tj, int tk) {
-    return sizeof(real) * (size_t)(5 * NVAR * (tj + 4) * (tk + 4) + NVAR * (tj + 1) * tk +
+    return sizeof(real) * (size_t)(6 * NVAR * (tj + 4) * (tk + 4) + NVAR * (tj + 1) * tk +
                                    NVAR * tj * (tk + 1) + 4 * (tj + 2) * (tk + 2));
   }
 };
@@ -51,14 +51,19 @@ __device__ __forceinline__ void flush_acc(const KParams &kp, double &acc, int me
   hits = 0;
 }
 
+// threads per CTA: the tile's cells rounded up to whole warps (the extra
+// threads own no cell but share the loads and the face fluxes)
+constexpr int stage_threads(int tj, int tk) { return (tj * tk + 31) / 32 * 32; }
+
 template <typename real, int TJ, int TK, bool S2>
-__global__ void __launch_bounds__(TJ *TK, (sizeof(real) == 4 ? 2 : 1))
+__global__ void __launch_bounds__(stage_threads(TJ, TK), (sizeof(real) == 4 ? 2 : 1))
     k_stage(const KParams kp, const StageLaunch sl) {
-  constexpr int NT = TJ * TK, RJ = TJ + 4, RK = TK + 4, RP = RJ * RK;
+  constexpr int NT = stage_threads(TJ, TK), RJ = TJ + 4, RK = TK + 4, RP = RJ * RK;
   constexpr int DJ = TJ + 2, DK = TK + 2, DP = DJ * DK;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   real *ring = reinterpret_cast<real *>(smem_raw);
-  real *fth = ring + 5 * NVAR * RP;
+  real *stage = ring + 5 * NVAR * RP;   // raw conserved variables of the next plane
+  real *fth = stage + NVAR * RP;
   real *fph = fth + NVAR * (TJ + 1) * TK;
   real *dring = fph + NVAR * TJ * (TK + 1);
 
@@ -72,6 +77,7 @@ __global__ void __launch_bounds__(TJ *TK, (sizeof(real) == 4 ? 2 : 1))
   const bool spherical = kp.geometry == 0;
   const real Om = (real)kp.omega, Cd = (real)kp.cd;
   const Isl isl{(float)kp.isl_pe, (float)kp.isl_beta};
+  const real igm1 = real(1) / (gamma - real(1));
 
   // reflux face buffer layout (per slot): faces in order r-lo, r-hi, th-lo,
   // th-hi, ph-lo, ph-hi; each [v][t1][t2]
@@ -104,23 +110,44 @@ __global__ void __launch_bounds__(TJ *TK, (sizeof(real) == 4 ? 2 : 1))
     const real *Uin = reinterpret_cast<const real *>(sl.Uin) + (size_t)slot * bstride;
     const real *U0 = reinterpret_cast<const real *>(sl.U0) + (size_t)slot * bstride;
     real *Uout = reinterpret_cast<real *>(sl.Uout) + (size_t)slot * bstride;
-    const bool valid = jl < nvj && kl < nvk;
+    const bool valid = tid < TJ * TK && jl < nvj && kl < nvk;
     const int j = j0 + jl, k = k0 + kl;           // interior indices in the block
     const int J = J0 + jl, K = K0 + kl;           // global indices at the level
 
-    auto load_plane = [&](int p) {
-      real *dst = ring + ((p + 5) % 5) * NVAR * RP;
+    // Planes are copied asynchronously (cp.async, 2 cells x 8 variables per
+    // unit) into the staging buffer one iteration ahead; the thread that
+    // copied a unit later converts it to primitives, so no barrier is needed
+    // between the copy and the conversion.
+    constexpr int HK = RK / 2, NU = RJ * HK;
+    auto issue_plane = [&](int p) {
       const real *src = Uin + (size_t)(p + NGH) * plane;
-      for (int q = tid; q < RP; q += NT) {
-        const int jj = q / RK, kk = q - (q / RK) * RK;
+      for (int u = tid; u < NU; u += NT) {
+        const int jj = u / HK, kk = 2 * (u - (u / HK) * HK);
         const int pj = j0 + jj, pk = k0 + kk;
         if (pj < P1 && pk < P2) {
-          real u[NVAR], wv[NVAR];
 #pragma unroll
-          for (int v = 0; v < NVAR; v++) u[v] = src[v * vstride + (size_t)pj * P2 + pk];
-          cons2prim<real>(u, wv, gamma, pfl, isl);
+          for (int v = 0; v < NVAR; v++)
+            cp_async<2 * sizeof(real)>(stage + v * RP + jj * RK + kk, src + v * vstride + (size_t)pj * P2 + pk);
+        }
+      }
+      cp_async_commit();
+    };
+    auto convert_plane = [&](int p) {
+      cp_async_wait_all();
+      real *dst = ring + ((p + 5) % 5) * NVAR * RP;
+      for (int u = tid; u < NU; u += NT) {
+        const int jj = u / HK, kk = 2 * (u - (u / HK) * HK);
+        if (j0 + jj < P1 && k0 + kk < P2) {
 #pragma unroll
-          for (int v = 0; v < NVAR; v++) dst[v * RP + q] = wv[v];
+          for (int h = 0; h < 2; h++) {
+            const int q = jj * RK + kk + h;
+            real uu[NVAR], wv[NVAR];
+#pragma unroll
+            for (int v = 0; v < NVAR; v++) uu[v] = stage[v * RP + q];
+            cons2prim<real>(uu, wv, gamma, pfl, isl);
+#pragma unroll
+            for (int v = 0; v < NVAR; v++) dst[v * RP + q] = wv[v];
+          }
         }
       }
     };
@@ -129,13 +156,24 @@ __global__ void __launch_bounds__(TJ *TK, (sizeof(real) == 4 ? 2 : 1))
 #pragma unroll
       for (int v = 0; v < NVAR; v++) w[v] = pl[v * RP + jj * RK + kk];
     };
-    auto rflux = [&](int p, real *F) {  // face between planes p-1 and p
-      real a[NVAR], b[NVAR], c[NVAR], e[NVAR];
-      gather(ringp(p - 2), jl + 2, kl + 2, a);
+    // limited radial slope at plane p of the thread's column
+    auto rslope = [&](int p, real *sl_) {
+      const real *pm = ringp(p - 1), *pc = ringp(p), *pp = ringp(p + 1);
+      const int o = (jl + 2) * RK + kl + 2;
+#pragma unroll
+      for (int v = 0; v < NVAR; v++) sl_[v] = mc_slope<real>(pm[v * RP + o], pc[v * RP + o], pp[v * RP + o]);
+    };
+    // radial face between planes p-1 and p from the slopes at both planes
+    auto rflux = [&](int p, const real *sm, const real *sp, real *F) {
+      real b[NVAR], c[NVAR], WL[NVAR], WR[NVAR];
       gather(ringp(p - 1), jl + 2, kl + 2, b);
       gather(ringp(p), jl + 2, kl + 2, c);
-      gather(ringp(p + 1), jl + 2, kl + 2, e);
-      tvdlf_face<real, 0>(a, b, c, e, gamma, F);
+#pragma unroll
+      for (int v = 0; v < NVAR; v++) {
+        WL[v] = b[v] + real(0.5) * sm[v];
+        WR[v] = c[v] - real(0.5) * sp[v];
+      }
+      tvdlf_states<real, 0>(WL, WR, b, c, gamma, igm1, F);
     };
     // div B at plane p on the (TJ+2) x (TK+2) positions around the tile
     auto divb_plane = [&](int p) {
@@ -143,6 +181,9 @@ __global__ void __launch_bounds__(TJ *TK, (sizeof(real) == 4 ? 2 : 1))
       const real *pm = ringp(p - 1), *pc = ringp(p), *pp = ringp(p + 1);
       const int I = I0 + p;
       const real rcm = G.rc[I - 1 + NGH], rcc = G.rc[I + NGH], rcp = G.rc[I + 1 + NGH];
+      // plane-uniform radial factors
+      const real wm = spherical ? rcm * rcm : real(1), wp = spherical ? rcp * rcp : real(1);
+      const real fr = RT<real>::rcp_((spherical ? rcc * rcc : real(1)) * (rcp - rcm));
       for (int q = tid; q < DP; q += NT) {
         const int dj = q / DK - 1, dk = q - (q / DK) * DK - 1;
         if (dj > nvj || dk > nvk) continue;
@@ -157,31 +198,46 @@ __global__ void __launch_bounds__(TJ *TK, (sizeof(real) == 4 ? 2 : 1))
         if (spherical) {
           const real stc = G.sintc[Jg + NGH];
           const real sm = G.sintc[Jg - 1 + NGH], sp = G.sintc[Jg + 1 + NGH];
-          div = (rcp * rcp * brp - rcm * rcm * brm) / (rcc * rcc * (rcp - rcm)) +
-                (sp * btp - sm * btm) / (rcc * stc * (tcp - tcm)) + (bpp - bpm) / (rcc * stc * (pcp - pcm));
+          const real irs = RT<real>::rcp_(rcc * stc);
+          div = (wp * brp - wm * brm) * fr + (sp * btp - sm * btm) * irs * RT<real>::rcp_(tcp - tcm) +
+                (bpp - bpm) * irs * RT<real>::rcp_(pcp - pcm);
         } else {
-          div = (brp - brm) / (rcp - rcm) + (btp - btm) / (tcp - tcm) + (bpp - bpm) / (pcp - pcm);
+          div = (brp - brm) * fr + (btp - btm) * RT<real>::rcp_(tcp - tcm) + (bpp - bpm) * RT<real>::rcp_(pcp - pcm);
         }
         dst[q] = div;
       }
     };
 
-    // ---- prologue: planes ib-2 .. ib+1 ----
-    for (int p = ib - 2; p <= ib + 1; p++) load_plane(p);
+    // ---- prologue: planes ib-2 .. ib+2 converted, ib+3 in flight ----
+    for (int p = ib - 2; p <= ib + 2; p++) {
+      issue_plane(p);
+      convert_plane(p);
+    }
+    if (ib + 3 <= ie + 1) issue_plane(ib + 3);
     __syncthreads();
     if (S2) {
       divb_plane(ib - 1);
       divb_plane(ib);
     }
-    real Flo[NVAR];
-    if (valid) rflux(ib, Flo);
+    real Flo[NVAR], sc[NVAR];
+    if (valid) {
+      real s0[NVAR];
+      rslope(ib - 1, s0);
+      rslope(ib, sc);
+      rflux(ib, s0, sc, Flo);
+    }
 
     for (int i = ib; i < ie; i++) {
-      load_plane(i + 2);
-      __syncthreads();
+      if (i > ib) __syncthreads();   // plane i+2 converted by every thread
       if (S2) divb_plane(i + 1);
       real Fhi[NVAR];
-      if (valid) rflux(i + 1, Fhi);
+      if (valid) {
+        real sn[NVAR];
+        rslope(i + 1, sn);
+        rflux(i + 1, sc, sn, Fhi);
+#pragma unroll
+        for (int v = 0; v < NVAR; v++) sc[v] = sn[v];
+      }
       // theta and phi faces of plane i
       {
         const real *pl = ringp(i);
@@ -195,7 +251,7 @@ __global__ void __launch_bounds__(TJ *TK, (sizeof(real) == 4 ? 2 : 1))
               gather(pl, row + 1, col + 2, b);
               gather(pl, row + 2, col + 2, c);
               gather(pl, row + 3, col + 2, e);
-              tvdlf_face<real, 1>(a, b, c, e, gamma, F);
+              tvdlf_face<real, 1>(a, b, c, e, gamma, igm1, F);
 #pragma unroll
               for (int v = 0; v < NVAR; v++) fth[(v * (TJ + 1) + row) * TK + col] = F[v];
             }
@@ -206,7 +262,7 @@ __global__ void __launch_bounds__(TJ *TK, (sizeof(real) == 4 ? 2 : 1))
               gather(pl, row + 2, col + 1, b);
               gather(pl, row + 2, col + 2, c);
               gather(pl, row + 2, col + 3, e);
-              tvdlf_face<real, 2>(a, b, c, e, gamma, F);
+              tvdlf_face<real, 2>(a, b, c, e, gamma, igm1, F);
 #pragma unroll
               for (int v = 0; v < NVAR; v++) fph[(v * TJ + row) * (TK + 1) + col] = F[v];
             }
@@ -223,7 +279,7 @@ __global__ void __launch_bounds__(TJ *TK, (sizeof(real) == 4 ? 2 : 1))
         const real Atm = G.sinf[iJ] * dr2 * dphi, Atp = G.sinf[iJ + 1] * dr2 * dphi;
         const real Ap = dr2 * G.dth[iJ];
         const real V = G.dr3[iI] * dcos * dphi;
-        const real iV = real(1) / V;
+        const real iV = RT<real>::rcp_(V);
         real w[NVAR];
         gather(ringp(i), jl + 2, kl + 2, w);
         real un[NVAR];
@@ -263,18 +319,20 @@ __global__ void __launch_bounds__(TJ *TK, (sizeof(real) == 4 ? 2 : 1))
           real gr_, gt_, gp_, h2inv;
           if (spherical) {
             const real st = G.sintc[iJ];
-            gr_ = (dp[q] - dm[q]) / (rcp - rcm);
-            gt_ = (dc[q + DK] - dc[q - DK]) / (rcc * (tcp - tcm));
-            gp_ = (dc[q + 1] - dc[q - 1]) / (rcc * st * (pcp - pcm));
-            const real xt = rcc * dth, xp = rcc * st * dphi;
-            h2inv = real(1) / (dr * dr) + real(1) / (xt * xt) + real(1) / (xp * xp);
+            const real irc = RT<real>::rcp_(rcc), irs = RT<real>::rcp_(rcc * st);
+            gr_ = (dp[q] - dm[q]) * RT<real>::rcp_(rcp - rcm);
+            gt_ = (dc[q + DK] - dc[q - DK]) * irc * RT<real>::rcp_(tcp - tcm);
+            gp_ = (dc[q + 1] - dc[q - 1]) * irs * RT<real>::rcp_(pcp - pcm);
+            const real idr = RT<real>::rcp_(dr), ixt = irc * RT<real>::rcp_(dth), ixp = irs * RT<real>::rcp_(dphi);
+            h2inv = idr * idr + ixt * ixt + ixp * ixp;
           } else {
-            gr_ = (dp[q] - dm[q]) / (rcp - rcm);
-            gt_ = (dc[q + DK] - dc[q - DK]) / (tcp - tcm);
-            gp_ = (dc[q + 1] - dc[q - 1]) / (pcp - pcm);
-            h2inv = real(1) / (dr * dr) + real(1) / (dth * dth) + real(1) / (dphi * dphi);
+            gr_ = (dp[q] - dm[q]) * RT<real>::rcp_(rcp - rcm);
+            gt_ = (dc[q + DK] - dc[q - DK]) * RT<real>::rcp_(tcp - tcm);
+            gp_ = (dc[q + 1] - dc[q - 1]) * RT<real>::rcp_(pcp - pcm);
+            const real idr = RT<real>::rcp_(dr), idt = RT<real>::rcp_(dth), idp = RT<real>::rcp_(dphi);
+            h2inv = idr * idr + idt * idt + idp * idp;
           }
-          const real f = Cd / h2inv;
+          const real f = Cd * RT<real>::rcp_(h2inv);
           const real dB0 = f * gr_, dB1 = f * gt_, dB2 = f * gp_;
           un[5] += dB0;
           un[6] += dB1;
@@ -299,9 +357,9 @@ __global__ void __launch_bounds__(TJ *TK, (sizeof(real) == 4 ? 2 : 1))
               dx1 *= G.rc[iI];
               dx2 *= G.rc[iI] * G.sintc[iJ];
             }
-            const real s = (RT<real>::abs_(wn[1]) + fast_speed<real, 0>(wn, gamma)) / dx0 +
-                           (RT<real>::abs_(wn[2]) + fast_speed<real, 1>(wn, gamma)) / dx1 +
-                           (RT<real>::abs_(wn[3]) + fast_speed<real, 2>(wn, gamma)) / dx2;
+            const real s = (RT<real>::abs_(wn[1]) + fast_speed<real, 0>(wn, gamma)) * RT<real>::rcp_(dx0) +
+                           (RT<real>::abs_(wn[2]) + fast_speed<real, 1>(wn, gamma)) * RT<real>::rcp_(dx1) +
+                           (RT<real>::abs_(wn[3]) + fast_speed<real, 2>(wn, gamma)) * RT<real>::rcp_(dx2);
             inv_acc = fmax(inv_acc, (double)s);
           }
           if (sl.flux) {
@@ -335,7 +393,11 @@ __global__ void __launch_bounds__(TJ *TK, (sizeof(real) == 4 ? 2 : 1))
 #pragma unroll
         for (int v = 0; v < NVAR; v++) Flo[v] = Fhi[v];
       }
+      // next plane: convert the one in flight, start the copy of the one after
+      if (i + 3 <= ie + 1) convert_plane(i + 3);
+      if (i + 4 <= ie + 1) issue_plane(i + 4);
     }
+    cp_async_wait_all();
     __syncthreads();  // shared memory is reused by the next work item
   }
   if (S2) flush_acc(kp, inv_acc, cur_member, hits);
@@ -356,9 +418,9 @@ int launch_t(const KParams &kp, const StageLaunch &sl, cudaStream_t s) {
     configured[0] = true;
   }
   if (sl.stage2)
-    k_stage<real, TJ, TK, true><<<sl.grid, TJ * TK, smem, s>>>(kp, sl);
+    k_stage<real, TJ, TK, true><<<sl.grid, stage_threads(TJ, TK), smem, s>>>(kp, sl);
   else
-    k_stage<real, TJ, TK, false><<<sl.grid, TJ * TK, smem, s>>>(kp, sl);
+    k_stage<real, TJ, TK, false><<<sl.grid, stage_threads(TJ, TK), smem, s>>>(kp, sl);
   return cudaPeekAtLastError() == cudaSuccess ? 0 : -1;
 }
 
@@ -368,6 +430,8 @@ int dispatch(const KParams &kp, const StageLaunch &sl, cudaStream_t s) {
   if (sl.tile_j == 12 && sl.tile_k == 12) return launch_t<real, 12, 12>(kp, sl, s);
   if (sl.tile_j == 8 && sl.tile_k == 32) return launch_t<real, 8, 32>(kp, sl, s);
   if (sl.tile_j == 4 && sl.tile_k == 32) return launch_t<real, 4, 32>(kp, sl, s);
+  if (sl.tile_j == 12 && sl.tile_k == 20) return launch_t<real, 12, 20>(kp, sl, s);
+  if (sl.tile_j == 6 && sl.tile_k == 36) return launch_t<real, 6, 36>(kp, sl, s);
   return -2;
 }
 
@@ -377,7 +441,7 @@ int occupancy_t() {
   const size_t smem = StageSmem<real>::bytes(TJ, TK);
   cudaFuncSetAttribute(k_stage<real, TJ, TK, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   cudaFuncSetAttribute(k_stage<real, TJ, TK, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_stage<real, TJ, TK, true>, TJ * TK, smem) != cudaSuccess)
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_stage<real, TJ, TK, true>, stage_threads(TJ, TK), smem) != cudaSuccess)
     return 1;
   return n > 0 ? n : 1;
 }
@@ -388,6 +452,8 @@ int occupancy(int tj, int tk) {
   if (tj == 12 && tk == 12) return occupancy_t<real, 12, 12>();
   if (tj == 8 && tk == 32) return occupancy_t<real, 8, 32>();
   if (tj == 4 && tk == 32) return occupancy_t<real, 4, 32>();
+  if (tj == 12 && tk == 20) return occupancy_t<real, 12, 20>();
+  if (tj == 6 && tk == 36) return occupancy_t<real, 6, 36>();
   return 1;
 }
 
@@ -395,7 +461,8 @@ int occupancy(int tj, int tk) {
 
 int stage_tile_supported(int precision, int tj, int tk) {
   (void)precision;
-  return (tj == 8 && tk == 8) || (tj == 12 && tk == 12) || (tj == 8 && tk == 32) || (tj == 4 && tk == 32);
+  return (tj == 8 && tk == 8) || (tj == 12 && tk == 12) || (tj == 8 && tk == 32) || (tj == 4 && tk == 32) ||
+         (tj == 12 && tk == 20) || (tj == 6 && tk == 36);
 }
 
 size_t stage_smem_bytes(int precision, int tj, int tk) {

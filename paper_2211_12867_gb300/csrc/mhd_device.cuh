@@ -16,12 +16,14 @@ template <> struct RT<double> {
   static __device__ __forceinline__ double abs_(double x) { return fabs(x); }
   static __device__ __forceinline__ double min_(double a, double b) { return fmin(a, b); }
   static __device__ __forceinline__ double max_(double a, double b) { return fmax(a, b); }
+  static __device__ __forceinline__ double rcp_(double x) { return __drcp_rn(x); }
 };
 template <> struct RT<float> {
   static __device__ __forceinline__ float sqrt_(float x) { return sqrtf(x); }
   static __device__ __forceinline__ float abs_(float x) { return fabsf(x); }
   static __device__ __forceinline__ float min_(float a, float b) { return fminf(a, b); }
   static __device__ __forceinline__ float max_(float a, float b) { return fmaxf(a, b); }
+  static __device__ __forceinline__ float rcp_(float x) { return __frcp_rn(x); }
 };
 
 // Pressure from conserved variables.  In the mixed-precision mode the FP32
@@ -35,7 +37,7 @@ struct Isl {
 
 template <typename real>
 __device__ __forceinline__ real pressure_of(const real *u, real gamma, Isl) {
-  real ir = real(1) / u[0];
+  real ir = RT<real>::rcp_(u[0]);
   real msq = u[1] * u[1] + u[2] * u[2] + u[3] * u[3];
   real me = real(0.5) * (u[5] * u[5] + u[6] * u[6] + u[7] * u[7]);
   real p = (gamma - real(1)) * (u[4] - real(0.5) * msq * ir - me);
@@ -59,7 +61,7 @@ __device__ __forceinline__ float pressure_fp64_island(const float *u, float gamm
 
 // float pressure without the island (accurate to ~1e-6 e)
 __device__ __forceinline__ float pressure_fp32(const float *u, float gamma) {
-  float ir = 1.0f / u[0];
+  float ir = __frcp_rn(u[0]);
   float msq = u[1] * u[1] + u[2] * u[2] + u[3] * u[3];
   float me = 0.5f * (u[5] * u[5] + u[6] * u[6] + u[7] * u[7]);
   return (gamma - 1.0f) * (u[4] - 0.5f * msq * ir - me);
@@ -87,7 +89,7 @@ __device__ __forceinline__ float pressure_for_speed<float>(const float *u, float
 // U -> W with the pressure floor of the stage operator.
 template <typename real>
 __device__ __forceinline__ void cons2prim(const real *u, real *w, real gamma, real pfloor, Isl isl) {
-  real ir = real(1) / u[0];
+  real ir = RT<real>::rcp_(u[0]);
   w[0] = u[0];
   w[1] = u[1] * ir;
   w[2] = u[2] * ir;
@@ -102,7 +104,7 @@ __device__ __forceinline__ void cons2prim(const real *u, real *w, real gamma, re
 // primitives for the CFL speed (no FP64 island in the FP32 mode)
 template <typename real>
 __device__ __forceinline__ void cons2prim_speed(const real *u, real *w, real gamma, real pfloor) {
-  real ir = real(1) / u[0];
+  real ir = RT<real>::rcp_(u[0]);
   w[0] = u[0];
   w[1] = u[1] * ir;
   w[2] = u[2] * ir;
@@ -115,14 +117,14 @@ __device__ __forceinline__ void cons2prim_speed(const real *u, real *w, real gam
 }
 
 template <typename real>
-__device__ __forceinline__ void prim2cons(const real *w, real *u, real gamma) {
+__device__ __forceinline__ void prim2cons(const real *w, real *u, real igm1) {
   real v2 = w[1] * w[1] + w[2] * w[2] + w[3] * w[3];
   real b2 = w[5] * w[5] + w[6] * w[6] + w[7] * w[7];
   u[0] = w[0];
   u[1] = w[0] * w[1];
   u[2] = w[0] * w[2];
   u[3] = w[0] * w[3];
-  u[4] = w[4] / (gamma - real(1)) + real(0.5) * w[0] * v2 + real(0.5) * b2;
+  u[4] = w[4] * igm1 + real(0.5) * w[0] * v2 + real(0.5) * b2;
   u[5] = w[5];
   u[6] = w[6];
   u[7] = w[7];
@@ -131,7 +133,7 @@ __device__ __forceinline__ void prim2cons(const real *w, real *u, real gamma) {
 // fast magnetosonic speed along direction D
 template <typename real, int D>
 __device__ __forceinline__ real fast_speed(const real *w, real gamma) {
-  real ir = real(1) / w[0];
+  real ir = RT<real>::rcp_(w[0]);
   real a2 = gamma * w[4] * ir;
   real b2 = (w[5] * w[5] + w[6] * w[6] + w[7] * w[7]) * ir;
   real bn2 = w[5 + D] * w[5 + D] * ir;
@@ -170,17 +172,12 @@ __device__ __forceinline__ void phys_flux(const real *w, real e, real *F) {
   F[4] = (e + pt) * vn - Bn * vB;
 }
 
-// TVDLF face flux from the four cells a, b | c, e around the face (primitive
-// variables); F receives the numerical flux.
+// TVDLF flux from reconstructed face states WL | WR (primitive variables);
+// b, c are the two cell values the face falls back to when a reconstructed
+// density or pressure is not positive.
 template <typename real, int D>
-__device__ __forceinline__ void tvdlf_face(const real *a, const real *b, const real *c, const real *e,
-                                           real gamma, real *F) {
-  real WL[NVAR], WR[NVAR];
-#pragma unroll
-  for (int v = 0; v < NVAR; v++) {
-    WL[v] = b[v] + real(0.5) * mc_slope<real>(a[v], b[v], c[v]);
-    WR[v] = c[v] - real(0.5) * mc_slope<real>(b[v], c[v], e[v]);
-  }
+__device__ __forceinline__ void tvdlf_states(real *WL, real *WR, const real *b, const real *c, real gamma,
+                                             real igm1, real *F) {
   if (!(WL[0] > real(0)) || !(WL[4] > real(0)) || !(WR[0] > real(0)) || !(WR[4] > real(0))) {
 #pragma unroll
     for (int v = 0; v < NVAR; v++) {
@@ -189,8 +186,8 @@ __device__ __forceinline__ void tvdlf_face(const real *a, const real *b, const r
     }
   }
   real UL[NVAR], UR[NVAR], FL[NVAR], FR[NVAR];
-  prim2cons<real>(WL, UL, gamma);
-  prim2cons<real>(WR, UR, gamma);
+  prim2cons<real>(WL, UL, igm1);
+  prim2cons<real>(WR, UR, igm1);
   phys_flux<real, D>(WL, UL[4], FL);
   phys_flux<real, D>(WR, UR[4], FR);
   real cl = RT<real>::abs_(WL[1 + D]) + fast_speed<real, D>(WL, gamma);
@@ -200,6 +197,32 @@ __device__ __forceinline__ void tvdlf_face(const real *a, const real *b, const r
   for (int v = 0; v < NVAR; v++) F[v] = real(0.5) * (FL[v] + FR[v]) - real(0.5) * cm * (UR[v] - UL[v]);
   F[5 + D] = real(0);
 }
+
+// TVDLF face flux from the four cells a, b | c, e around the face (primitive
+// variables); F receives the numerical flux.
+template <typename real, int D>
+__device__ __forceinline__ void tvdlf_face(const real *a, const real *b, const real *c, const real *e,
+                                           real gamma, real igm1, real *F) {
+  real WL[NVAR], WR[NVAR];
+#pragma unroll
+  for (int v = 0; v < NVAR; v++) {
+    WL[v] = b[v] + real(0.5) * mc_slope<real>(a[v], b[v], c[v]);
+    WR[v] = c[v] - real(0.5) * mc_slope<real>(b[v], c[v], e[v]);
+  }
+  tvdlf_states<real, D>(WL, WR, b, c, gamma, igm1, F);
+}
+
+// asynchronous global -> shared copies of 8 or 16 bytes (cp.async)
+template <int BYTES>
+__device__ __forceinline__ void cp_async(void *smem, const void *gmem) {
+  const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+  if (BYTES == 16)
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(s), "l"(gmem) : "memory");
+  else
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(s), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;\n" ::: "memory"); }
 
 // floors on a freshly updated cell; returns the number of floor hits
 template <typename real>

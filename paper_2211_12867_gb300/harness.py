@@ -1,0 +1,196 @@
+"""Run driver: relaxation, cone-CME injection, propagation with regrids and
+probes at Earth, and the arrival-time analysis.
+
+The paper relaxes the wind until the slow stream has crossed the domain,
+injects the cone CME through the inner boundary (Sect. 2.1, Eqs. 1-4) and
+reads time series at Earth (Figs. 1, 3, 6, 9); it reports the shock arrival
+time and the shock width, the time from arrival to the peak speed
+(Sect. 3.1).  Arrival is read here as the first sample where the radial speed
+exceeds the background at the same point by 50 km/s, linearly interpolated to
+the crossing; the background is the relaxed state sampled along Earth's path
+(steady in the co-rotating frame).  All device work goes through the C ABI
+(``icarus.Icarus``).
+"""
+from __future__ import annotations
+
+import math
+from dataclasses import dataclass, field
+
+import numpy as np
+
+from . import inputs as I
+
+
+# ---------------------------------------------------------------- analysis
+def arrival_time(t, vr, vbg, dv=I.kms(50.0)):
+    """First crossing of vr - vbg above dv (linear interpolation between
+    samples); None if the series never crosses."""
+    t, vr, vbg = (np.asarray(x, dtype=np.float64) for x in (t, vr, vbg))
+    ex = vr - vbg - dv
+    above = np.nonzero(ex > 0.0)[0]
+    if len(above) == 0:
+        return None
+    k = above[0]
+    if k == 0:
+        return float(t[0])
+    a, b = ex[k - 1], ex[k]
+    return float(t[k - 1] + (t[k] - t[k - 1]) * (-a) / (b - a))
+
+
+def shock_width(t, vr, t_arr, window=None):
+    """Time from arrival to the peak radial speed within `window` after it
+    (default 24 h)."""
+    if t_arr is None:
+        return None
+    window = I.hours(24.0) if window is None else window
+    t, vr = np.asarray(t), np.asarray(vr)
+    sel = (t >= t_arr) & (t <= t_arr + window)
+    if not np.any(sel):
+        return None
+    k = np.argmax(np.where(sel, vr, -np.inf))
+    return float(t[k] - t_arr)
+
+
+def peak_speed(t, vr, t_arr, window=None):
+    if t_arr is None:
+        return None
+    window = I.hours(24.0) if window is None else window
+    t, vr = np.asarray(t), np.asarray(vr)
+    sel = (t >= t_arr) & (t <= t_arr + window)
+    return float(np.max(vr[sel])) if np.any(sel) else None
+
+
+# ---------------------------------------------------------------- learned pre-flagger
+def _related(tree_a, tree_b):
+    """For each leaf of tree_b, the indices of tree_a leaves overlapping it
+    (a regrid changes a region by at most one level: self, parent or the 8
+    children)."""
+    index = {(int(l), int(i), int(j), int(k)): n for n, (l, i, j, k) in enumerate(tree_a)}
+    out = []
+    for (l, i, j, k) in tree_b:
+        l, i, j, k = int(l), int(i), int(j), int(k)
+        hit = []
+        if (l, i, j, k) in index:
+            hit.append(index[(l, i, j, k)])
+        if (l - 1, i >> 1, j >> 1, k >> 1) in index:
+            hit.append(index[(l - 1, i >> 1, j >> 1, k >> 1)])
+        for c in range(8):
+            key = (l + 1, 2 * i + (c >> 2 & 1), 2 * j + (c >> 1 & 1), 2 * k + (c & 1))
+            if key in index:
+                hit.append(index[key])
+        out.append(hit)
+    return out
+
+
+def next_regrid_labels(tree_k, tree_k1, flags_k1):
+    """Label of each leaf at regrid k: 1 if the plain estimator flags any
+    overlapping leaf for refinement at regrid k+1."""
+    lab = np.zeros(len(tree_k), dtype=np.float32)
+    for hits, f in zip(_related(tree_k, tree_k1), flags_k1):
+        if f > 0:
+            lab[hits] = 1.0
+    return lab
+
+
+def missed_flag_rate(tree_k, preflag_k, tree_k1, flags_k1):
+    """Fraction of leaves flagged +1 by the plain estimator at regrid k+1 whose
+    region was not pre-flagged at regrid k (None if nothing was flagged)."""
+    need = missed = 0
+    for hits, f in zip(_related(tree_k, tree_k1), flags_k1):
+        if f > 0:
+            need += 1
+            if not any(preflag_k[h] for h in hits):
+                missed += 1
+    return (missed / need) if need else None
+
+
+def collect_regrids(g, n_regrids, regrid_every, t_stop=np.inf, crit=None):
+    """Advance with plain regrids and record, at every regrid, the tree of
+    member 0, the features of its leaves and the plain flags."""
+    recs = []
+    for _ in range(n_regrids):
+        g.step(regrid_every, t_stop=t_stop)
+        feats = g.mlp_features()
+        flags = g.flag_refine(**(crit or {}))
+        n0 = g.n_leaves(0)
+        recs.append({"tree": g.tree(0), "feat": feats[:n0].copy(), "flags": flags[:n0].copy()})
+        g.regrid()
+    return recs
+
+
+def training_pairs(recs):
+    """(features at regrid k, label from the plain flags at regrid k+1)"""
+    X, T = [], []
+    for a, b in zip(recs[:-1], recs[1:]):
+        X.append(a["feat"])
+        T.append(next_regrid_labels(a["tree"], b["tree"], b["flags"]))
+    return np.concatenate(X), np.concatenate(T)
+
+
+# ---------------------------------------------------------------- driver
+@dataclass
+class RunResult:
+    times: np.ndarray
+    series: np.ndarray          # [member][sample][8] primitives at Earth
+    background: np.ndarray      # [member][sample][8]
+    arrival: list
+    width: list
+    peak: list
+    steps: int = 0
+    regrids: int = 0
+    leaves: list = field(default_factory=list)   # leaves per regrid (all members)
+    wall_s: float = 0.0
+
+
+def advance_to(g, t_target, max_steps=1_000_000, regrid_every=0, crit=None, counters=None,
+               on_regrid=None):
+    """Step every member until it reaches t_target (regridding every
+    `regrid_every` steps when > 0)."""
+    n = 0
+    chunk = regrid_every if regrid_every > 0 else 200
+    while True:
+        t = g.step(chunk, t_stop=t_target)
+        n += chunk
+        if counters is not None:
+            counters["steps"] += chunk
+        if np.all(t >= t_target) or n >= max_steps:
+            return t
+        if regrid_every > 0:
+            flags = g.flag_refine(**(crit or {}))
+            if on_regrid is not None:
+                flags = on_regrid(g, flags)
+                g.set_flags(flags)
+            g.regrid()
+            if counters is not None:
+                counters["regrids"] += 1
+                counters["leaves"].append(g.n_leaves(-1))
+
+
+def propagate(g, cmes, *, t_inj, duration, sample=None, earth_lon0=math.pi, regrid_every=0, crit=None,
+              on_regrid=None):
+    """Inject one cone CME per member at t_inj and record Earth time series
+    every `sample` (default 10 min) for `duration`; returns RunResult."""
+    import time as _time
+    sample = I.hours(1.0 / 6.0) if sample is None else sample
+    nm = g.n_members
+    times = t_inj + sample * np.arange(int(round(duration / sample)) + 1)
+    pts = np.stack([I.earth_position(t, t_inj, earth_lon0) for t in times])
+    bg = np.stack([g.probe(m, pts) for m in range(nm)])
+    for m, c in enumerate(cmes):
+        g.inject_cone_cme(m, t_start=t_inj, **{k: v for k, v in c.items() if k in
+                                               ("t_max", "colat", "lon", "half_width", "v", "rho", "p")})
+    series = np.zeros((nm, len(times), 8))
+    for m in range(nm):
+        series[m, 0] = g.probe(m, pts[:1])[0]
+    counters = {"steps": 0, "regrids": 0, "leaves": []}
+    w0 = _time.perf_counter()
+    for k in range(1, len(times)):
+        advance_to(g, times[k], regrid_every=regrid_every, crit=crit, counters=counters, on_regrid=on_regrid)
+        for m in range(nm):
+            series[m, k] = g.probe(m, pts[k:k + 1])[0]
+    wall = _time.perf_counter() - w0
+    arr = [arrival_time(times, series[m, :, 1], bg[m, :, 1]) for m in range(nm)]
+    wid = [shock_width(times, series[m, :, 1], a) for m, a in zip(range(nm), arr)]
+    pk = [peak_speed(times, series[m, :, 1], a) for m, a in zip(range(nm), arr)]
+    return RunResult(times, series, bg, arr, wid, pk, counters["steps"], counters["regrids"],
+                     counters["leaves"], wall)

@@ -34,7 +34,10 @@ EXPORTS = [
     "icarus_n_leaves", "icarus_get_tree", "icarus_set_state", "icarus_get_state", "icarus_set_time",
     "icarus_set_member_max_level", "icarus_ghost_fill", "icarus_conservation_sums", "icarus_get_dt",
     "icarus_status_word", "icarus_set_tile", "icarus_use_graph", "icarus_kernels_per_step",
-    "icarus_profile", "icarus_profile_read", "icarus_set_fp64_islands", "icarus_destroy",
+    "icarus_profile", "icarus_profile_read", "icarus_set_fp64_islands", "icarus_conservation_sums_static",
+    "icarus_mlp_set_params", "icarus_mlp_get_params", "icarus_mlp_features", "icarus_mlp_predict_leaves",
+    "icarus_mlp_predict", "icarus_mlp_grad", "icarus_mlp_dataset_clear", "icarus_mlp_dataset_add",
+    "icarus_mlp_train", "icarus_destroy",
     "icarus_status_string",
 ]
 
@@ -301,6 +304,74 @@ class Icarus:
                                                                  cnt.ctypes.data_as(C.POINTER(C.c_int)), 7))
         return ms, cnt
 
+
+    # ---------------------------------------------------------------- learned pre-flagger
+    def _mlp(self, name, *argtypes):
+        f = getattr(self.lib, name)
+        f.restype = C.c_int
+        f.argtypes = [C.c_void_p] + list(argtypes)
+        return f
+
+    def mlp_set_params(self, theta):
+        th = np.ascontiguousarray(theta, dtype=np.float32)
+        _chk("icarus_mlp_set_params", self._mlp("icarus_mlp_set_params", C.c_void_p, C.c_size_t)(
+            self.ctx, th.ctypes.data_as(C.c_void_p), th.size))
+
+    def mlp_get_params(self):
+        th = np.zeros(MLP_PARAMS, dtype=np.float32)
+        _chk("icarus_mlp_get_params", self._mlp("icarus_mlp_get_params", C.c_void_p, C.c_size_t)(
+            self.ctx, th.ctypes.data_as(C.c_void_p), th.size))
+        return th
+
+    def mlp_features(self):
+        out = np.zeros((self.n_leaves(-1), 64), dtype=np.float32)
+        _chk("icarus_mlp_features", self._mlp("icarus_mlp_features", C.c_void_p)(
+            self.ctx, out.ctypes.data_as(C.c_void_p)))
+        return out
+
+    def mlp_predict_leaves(self):
+        out = np.zeros(self.n_leaves(-1), dtype=np.float32)
+        _chk("icarus_mlp_predict_leaves", self._mlp("icarus_mlp_predict_leaves", C.c_void_p)(
+            self.ctx, out.ctypes.data_as(C.c_void_p)))
+        return out
+
+    def mlp_predict(self, X):
+        X = np.ascontiguousarray(X, dtype=np.float32).reshape(-1, 64)
+        y = np.zeros(X.shape[0], dtype=np.float32)
+        _chk("icarus_mlp_predict", self._mlp("icarus_mlp_predict", C.c_void_p, C.c_int, C.c_void_p)(
+            self.ctx, X.ctypes.data_as(C.c_void_p), X.shape[0], y.ctypes.data_as(C.c_void_p)))
+        return y
+
+    def mlp_grad(self, X, T):
+        X = np.ascontiguousarray(X, dtype=np.float32).reshape(-1, 64)
+        T = np.ascontiguousarray(T, dtype=np.float32)
+        g = np.zeros(MLP_PARAMS, dtype=np.float32)
+        loss = C.c_float(0)
+        f = self._mlp("icarus_mlp_grad", C.c_void_p, C.c_void_p, C.c_int, C.c_void_p, C.POINTER(C.c_float))
+        _chk("icarus_mlp_grad", f(self.ctx, X.ctypes.data_as(C.c_void_p), T.ctypes.data_as(C.c_void_p), X.shape[0],
+                                  g.ctypes.data_as(C.c_void_p), C.byref(loss)))
+        return g, loss.value
+
+    def mlp_dataset_clear(self):
+        _chk("icarus_mlp_dataset_clear", self._mlp("icarus_mlp_dataset_clear")(self.ctx))
+
+    def mlp_dataset_add(self, X, T):
+        X = np.ascontiguousarray(X, dtype=np.float32).reshape(-1, 64)
+        T = np.ascontiguousarray(T, dtype=np.float32)
+        tot = C.c_int(0)
+        f = self._mlp("icarus_mlp_dataset_add", C.c_void_p, C.c_void_p, C.c_int, C.POINTER(C.c_int))
+        _chk("icarus_mlp_dataset_add", f(self.ctx, X.ctypes.data_as(C.c_void_p), T.ctypes.data_as(C.c_void_p),
+                                         X.shape[0], C.byref(tot)))
+        return tot.value
+
+    def mlp_train(self, n_train, epochs, batch=1024, lr=1e-3, seed=0):
+        losses = np.zeros(max(epochs, 1), dtype=np.float32)
+        f = self._mlp("icarus_mlp_train", C.c_int, C.c_int, C.c_int, C.c_double, C.c_uint64, C.c_void_p)
+        _chk("icarus_mlp_train", f(self.ctx, n_train, epochs, batch, lr, seed, losses.ctypes.data_as(C.c_void_p)))
+        return losses[:epochs] / n_train
+
+
+MLP_PARAMS = 128 * 64 + 128 + 128 * 128 + 128 + 128 + 1
 
 PROFILE_KINDS = ["dt_begin", "ghost_neighbour", "ghost_physical", "stage_predictor", "stage_corrector",
                  "reflux", "dt_finalize"]

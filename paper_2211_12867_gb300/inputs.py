@@ -190,3 +190,17 @@ def earth_position(t, t_inj, earth_lon0=math.pi, r=1.0):
     drifting at the synodic rate."""
     return np.array([r, 0.5 * math.pi,
                      (earth_lon0 - OMEGA_SYN * (t - t_inj)) % (2 * math.pi)])
+
+
+# ---------------------------------------------------------------- MLP init
+MLP_IN, MLP_H = 64, 128
+
+
+def mlp_init(seed):
+    """He-normal initial weights of the 64-128-128-1 refinement predictor,
+    zero biases (seeded); layout W1[128,64], b1, W2[128,128], b2, w3[128], b3."""
+    rng = np.random.default_rng(seed)
+    W1 = rng.normal(0.0, math.sqrt(2.0 / MLP_IN), (MLP_H, MLP_IN))
+    W2 = rng.normal(0.0, math.sqrt(2.0 / MLP_H), (MLP_H, MLP_H))
+    w3 = rng.normal(0.0, math.sqrt(2.0 / MLP_H), MLP_H)
+    return np.concatenate([W1.ravel(), np.zeros(MLP_H), W2.ravel(), np.zeros(MLP_H), w3, [0.0]])

