@@ -65,6 +65,15 @@ def parse():
     p.add_argument("--islands", default="0.002,0.1",
                    help="FP32 mode: FP64 pressure where p < a*e or p < b*B^2/2 ('a,b')")
     p.add_argument("--tile", default="", help="force the stage tile 'tile_theta,tile_phi,r_segment'")
+    p.add_argument("--workload", default="wedge", choices=["wedge", "amr", "ensemble", "tt1au"],
+                   help="amr / ensemble / tt1au: stretched AMR CME runs (one JSON line of their own)")
+    p.add_argument("--members", type=int, default=32)
+    p.add_argument("--max-blocks", type=int, default=60000)
+    p.add_argument("--train-regrids", type=int, default=60)
+    p.add_argument("--max-level", type=int, default=4)
+    p.add_argument("--hours", type=float, default=72.0)
+    p.add_argument("--relax-days", type=float, default=10.0)
+    p.add_argument("--regrid-every", type=int, default=10)
     p.add_argument("--mode", default="full", choices=["full", "kernel"],
                    help="kernel: set up and run warmup + steps only (for profiler captures)")
     return p.parse_args()
@@ -211,10 +220,114 @@ def run_reference(args):
     return 0
 
 
+def run_amr_workload(args):
+    """Stretched 264x36x96 grid with AMR (levels <= 4): relax 10 days, inject
+    the 512x60x180 workload's cone CME, propagate with regrids every 10 steps
+    and Earth probes every 10 minutes.  Prints one JSON line (not the
+    headline metric line)."""
+    import torch
+    from paper_2211_12867_gb300 import workloads as WL
+    from paper_2211_12867_gb300.icarus import FP32_MIXED, FP64, set_fp64_islands
+    torch.cuda.set_device(0)
+    prec = FP32_MIXED if args.precision == "fp32" else FP64
+    g = WL.amr_grid(n_members=1, max_level=args.max_level, precision=prec)
+    if prec == FP32_MIXED:
+        set_fp64_islands(g, *(float(x) for x in args.islands.split(",")))
+    WL.start_wind(g)
+    t_inj, wall_relax = WL.relax(g, args.relax_days)
+    cme = I.cme_config2(seed=0)
+    ups0 = float(np.sum(g.cell_updates()))
+    res = WL.run_cme(g, [cme], t_inj=t_inj, hours_after=args.hours, regrid_every=args.regrid_every)
+    rep = WL.amr_report(g, res, wall_relax, t_inj, ups0)
+    line = {"workload": "amr264x36x96_L%d" % args.max_level, "precision": args.precision, **rep}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def run_ensemble_workload(args):
+    """Ensemble of cone-CME draws on the stretched AMR grid, all members in
+    the same launches; members' finest levels 3 or 4 from the draws."""
+    import torch
+    from paper_2211_12867_gb300 import workloads as WL
+    from paper_2211_12867_gb300.icarus import FP32_MIXED
+    torch.cuda.set_device(0)
+    draws = I.cme_ensemble(args.members)
+    g = WL.amr_grid(n_members=args.members, max_level=4, precision=FP32_MIXED, max_blocks=args.max_blocks)
+    WL.start_wind(g)
+    t_inj, wall_relax = WL.relax(g, args.relax_days)
+    ups0 = float(np.sum(g.cell_updates()))
+    res = WL.run_cme(g, draws, t_inj=t_inj, hours_after=args.hours, regrid_every=args.regrid_every,
+                     max_levels=[d["max_level"] for d in draws])
+    rep = WL.amr_report(g, res, wall_relax, t_inj, ups0)
+    print(json.dumps({"workload": f"ensemble{args.members}_amr264x36x96", "precision": "fp32",
+                      "hours_after_injection": args.hours, "max_levels": [d["max_level"] for d in draws], **rep}),
+          flush=True)
+    return 0
+
+
+def run_tt1au_workload(args):
+    """Time to 1 AU: the plain FP64 single instance against the FP32 path with
+    the learned pre-flagger (trained on a separate run's regrids) at a doubled
+    regrid interval; wall clock from injection to the simulated arrival."""
+    import torch
+    from paper_2211_12867_gb300 import harness as H
+    from paper_2211_12867_gb300 import workloads as WL
+    from paper_2211_12867_gb300.icarus import FP32_MIXED, FP64
+    torch.cuda.set_device(0)
+    L = args.max_level
+    # training data: FP32 run with a different CME draw
+    g = WL.amr_grid(max_level=L, precision=FP32_MIXED, max_blocks=args.max_blocks)
+    WL.start_wind(g)
+    t_inj, _ = WL.relax(g, args.relax_days)
+    g.inject_cone_cme(0, t_start=t_inj, **I.cme_config2(seed=7))
+    # labels one regrid ahead at the interval the learned run uses
+    recs = H.collect_regrids(g, n_regrids=args.train_regrids, regrid_every=2 * args.regrid_every, crit=WL.CRIT)
+    X, T = H.training_pairs(recs)
+    if len(T) > 65536:   # the device dataset holds 65536 pairs: seeded subsample
+        sel = np.sort(np.random.default_rng(2).choice(len(T), 65536, replace=False))
+        X, T = X[sel], T[sel]
+    g.mlp_set_params(I.mlp_init(5).astype(np.float32))
+    g.mlp_dataset_clear()
+    g.mlp_dataset_add(X, T)
+    w0 = time.perf_counter()
+    losses = g.mlp_train(len(T), epochs=100, batch=1024, lr=1e-3, seed=1)
+    train_s = time.perf_counter() - w0
+    theta = g.mlp_get_params()
+    del g
+    out = {}
+    for name, prec, learned, every in (("fp32_learned", FP32_MIXED, True, 2 * args.regrid_every),
+                                       ("fp64_plain", FP64, False, args.regrid_every)):
+        g = WL.amr_grid(max_level=L, precision=prec, max_blocks=args.max_blocks)
+        if learned:
+            g.mlp_set_params(theta)
+        WL.start_wind(g)
+        t_inj, wall_relax = WL.relax(g, args.relax_days)
+        ups0 = float(np.sum(g.cell_updates()))
+        res = WL.run_cme(g, [I.cme_config2(seed=0)], t_inj=t_inj, hours_after=args.hours, regrid_every=every,
+                         learned=learned)
+        rep = WL.amr_report(g, res, wall_relax, t_inj, ups0)
+        arr = res.arrival[0]
+        if arr is not None:   # wall clock to the arrival sample, by linear share of the run
+            rep["time_to_arrival_s"] = res.wall_s * (arr - t_inj) / (res.times[-1] - t_inj)
+        out[name] = rep
+        del g
+    a32, a64 = out["fp32_learned"]["arrival_h"][0], out["fp64_plain"]["arrival_h"][0]
+    print(json.dumps({"workload": f"tt1au_amr264x36x96_L{L}", "train_pairs": int(len(T)),
+                      "train_loss": [float(losses[0]), float(losses[-1])], "train_s": train_s, **out,
+                      "arrival_diff_h": None if (a32 is None or a64 is None) else abs(a32 - a64)}), flush=True)
+    return 0
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         return run_reference(args)
+    if args.workload == "amr":
+        return run_amr_workload(args)
+    if args.workload == "ensemble":
+        return run_ensemble_workload(args)
+    if args.workload == "tt1au":
+        return run_tt1au_workload(args)
     import torch
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))

@@ -222,6 +222,11 @@ icarus_status icarus_conservation_sums_static(icarus_ctx *ctx, int member, doubl
 /* Current CFL time step of every member (host, n_members doubles). */
 icarus_status icarus_get_dt(icarus_ctx *ctx, double *dt_out);
 
+/* Cumulative leaf-cell updates of every member (a cell advanced by one full
+ * step counts once; members past their stop time do not count).  Host,
+ * n_members doubles.  Synchronises. */
+icarus_status icarus_cell_updates(icarus_ctx *ctx, double *out);
+
 /* Sticky device status word: bit 0 NaN seen, bit 1 floor budget exceeded,
  * bit 2 bounded wait gave up; *floor_hits receives the floor counter. */
 icarus_status icarus_status_word(icarus_ctx *ctx, uint32_t *word, uint64_t *floor_hits);

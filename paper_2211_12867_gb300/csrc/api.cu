@@ -136,7 +136,7 @@ Layout make_layout(const icarus_grid_desc *d) {
   L.bmap = L.add((size_t)nm * NVAR * d->n_cells[1] * d->n_cells[2] * sizeof(double));
   L.cme = L.add((size_t)nm * sizeof(DevCme));
   L.vbg = L.add((size_t)nm * d->n_cells[0] * d->n_cells[1] * d->n_cells[2] * sizeof(double));
-  L.scal = L.add((size_t)nm * 5 * sizeof(double) + 64);
+  L.scal = L.add((size_t)nm * 7 * sizeof(double) + 64);
   L.flags = L.add(mb);
   L.lists = L.add(2 * mb * sizeof(int));        // all-leaf list + per-level lists
   L.sides = L.add(6 * mb * sizeof(int2));       // (slot, side) per level, per direction
@@ -212,7 +212,8 @@ struct icarus_ctx {
   double *bmap = nullptr, *vbg = nullptr, *staging = nullptr, *partial = nullptr, *probe_in = nullptr,
          *probe_out = nullptr;
   DevCme *cme = nullptr;
-  double *t = nullptr, *dt_used = nullptr, *dt_cfl = nullptr, *tstop = nullptr;
+  double *t = nullptr, *dt_used = nullptr, *dt_cfl = nullptr, *tstop = nullptr, *updates = nullptr,
+         *cells_m = nullptr;
   unsigned long long *inv_max = nullptr, *floor_hits = nullptr;
   unsigned int *status = nullptr;
   signed char *flags = nullptr;
@@ -432,6 +433,13 @@ icarus_status upload_tree(icarus_ctx *c, DevBlock *blk_dst) {
       sv.insert(sv.end(), sd[k][L].begin(), sd[k][L].end());
     }
   c->nrlist = (int)rl.size();
+  {
+    std::vector<double> cm(d.n_members);
+    for (int m = 0; m < d.n_members; m++)
+      cm[m] = (double)c->mem[m].leaves.size() * d.block[0] * d.block[1] * d.block[2];
+    CK(cudaMemcpyAsync(c->cells_m, cm.data(), sizeof(double) * cm.size(), cudaMemcpyHostToDevice, c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+  }
   cudaStream_t s = c->stream;
   CK(cudaMemcpyAsync(blk_dst, c->hblk.data(), sizeof(DevBlock) * c->nleaves, cudaMemcpyHostToDevice, s));
   CK(cudaMemcpyAsync(c->lmap, lm.data(), sizeof(int) * lm.size(), cudaMemcpyHostToDevice, s));
@@ -479,6 +487,8 @@ void fill_kp(icarus_ctx *c) {
   k.t = c->t;
   k.dt_used = c->dt_used;
   k.dt_cfl = c->dt_cfl;
+  k.updates = c->updates;
+  k.cells_m = c->cells_m;
   k.inv_max = c->inv_max;
   k.status = c->status;
   k.floor_hits = c->floor_hits;
@@ -895,6 +905,8 @@ icarus_status icarus_init_grid(const icarus_grid_desc *desc, icarus_ctx **out) {
   c->inv_max = reinterpret_cast<unsigned long long *>(sc + 4 * nm);
   c->status = reinterpret_cast<unsigned int *>(sc + 5 * nm);
   c->floor_hits = reinterpret_cast<unsigned long long *>(sc + 5 * nm + 1);
+  c->updates = sc + 5 * nm + 2;
+  c->cells_m = sc + 6 * nm + 2;
   c->flags = at<signed char>(c, lay.flags);
   c->all_list = at<int>(c, lay.lists);
   c->lvl_list = c->all_list + lay.max_blocks;
@@ -1192,6 +1204,13 @@ icarus_status icarus_get_state(icarus_ctx *c, int member, double *host, size_t n
 icarus_status icarus_get_dt(icarus_ctx *c, double *dt) {
   if (!c || !dt) return ICARUS_ERR_ARG;
   CK(cudaMemcpyAsync(dt, c->dt_cfl, sizeof(double) * c->d.n_members, cudaMemcpyDeviceToHost, c->stream));
+  CK(cudaStreamSynchronize(c->stream));
+  return ICARUS_OK;
+}
+
+icarus_status icarus_cell_updates(icarus_ctx *c, double *out) {
+  if (!c || !out) return ICARUS_ERR_ARG;
+  CK(cudaMemcpyAsync(out, c->updates, sizeof(double) * c->d.n_members, cudaMemcpyDeviceToHost, c->stream));
   CK(cudaStreamSynchronize(c->stream));
   return ICARUS_OK;
 }

@@ -90,6 +90,8 @@ struct KParams {
   double *t;                   // [member]
   double *dt_used;             // [member]
   double *dt_cfl;              // [member]
+  double *updates;             // [member] cumulative leaf-cell updates
+  const double *cells_m;       // [member] leaf cells of the member
   unsigned long long *inv_max; // [member] bit pattern of a positive double
   unsigned int *status;
   unsigned long long *floor_hits;

@@ -362,6 +362,7 @@ __global__ void k_dt_finalize(const KParams kp, double cfl) {
   const double dt = kp.dt_used[m];
   if (dt > 0.0) {
     kp.t[m] += dt;
+    kp.updates[m] += kp.cells_m[m];
     const double inv = __longlong_as_double((long long)kp.inv_max[m]);
     if (inv > 0.0) kp.dt_cfl[m] = cfl / inv;
   }

@@ -92,11 +92,14 @@ def next_regrid_labels(tree_k, tree_k1, flags_k1):
     return lab
 
 
-def missed_flag_rate(tree_k, preflag_k, tree_k1, flags_k1):
+def missed_flag_rate(tree_k, preflag_k, tree_k1, flags_k1, max_level=None):
     """Fraction of leaves flagged +1 by the plain estimator at regrid k+1 whose
-    region was not pre-flagged at regrid k (None if nothing was flagged)."""
+    region was not pre-flagged at regrid k (None if nothing was flagged).
+    With `max_level`, only flagged leaves that can still refine count."""
     need = missed = 0
-    for hits, f in zip(_related(tree_k, tree_k1), flags_k1):
+    for (l, _, _, _), hits, f in zip(tree_k1, _related(tree_k, tree_k1), flags_k1):
+        if max_level is not None and l >= max_level:
+            continue
         if f > 0:
             need += 1
             if not any(preflag_k[h] for h in hits):
@@ -146,24 +149,32 @@ def advance_to(g, t_target, max_steps=1_000_000, regrid_every=0, crit=None, coun
                on_regrid=None):
     """Step every member until it reaches t_target (regridding every
     `regrid_every` steps when > 0)."""
+    counters = counters if counters is not None else {"steps": 0, "regrids": 0, "leaves": []}
+    counters.setdefault("since", 0)
+    cells_per_block = int(np.prod(g.block))
     n = 0
-    chunk = regrid_every if regrid_every > 0 else 200
     while True:
-        t = g.step(chunk, t_stop=t_target)
-        n += chunk
-        if counters is not None:
-            counters["steps"] += chunk
-        if np.all(t >= t_target) or n >= max_steps:
-            return t
-        if regrid_every > 0:
+        k = max(1, regrid_every - counters["since"]) if regrid_every > 0 else 500
+        u0 = g.cell_updates()
+        t = g.step(k, t_stop=t_target)
+        du = g.cell_updates() - u0
+        # steps actually taken (a member stops at t_target): from the exact
+        # per-member cell-update counters, no regrid in between
+        taken = max(int(round(du[m] / (g.n_leaves(m) * cells_per_block))) for m in range(g.n_members))
+        n += taken
+        counters["steps"] += taken
+        counters["since"] += taken
+        if regrid_every > 0 and counters["since"] >= regrid_every:
             flags = g.flag_refine(**(crit or {}))
             if on_regrid is not None:
                 flags = on_regrid(g, flags)
                 g.set_flags(flags)
             g.regrid()
-            if counters is not None:
-                counters["regrids"] += 1
-                counters["leaves"].append(g.n_leaves(-1))
+            counters["since"] = 0
+            counters["regrids"] += 1
+            counters["leaves"].append(g.n_leaves(-1))
+        if np.all(t >= t_target) or n >= max_steps or taken == 0:
+            return t
 
 
 def propagate(g, cmes, *, t_inj, duration, sample=None, earth_lon0=math.pi, regrid_every=0, crit=None,

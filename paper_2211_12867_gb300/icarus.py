@@ -37,7 +37,7 @@ EXPORTS = [
     "icarus_profile", "icarus_profile_read", "icarus_set_fp64_islands", "icarus_conservation_sums_static",
     "icarus_mlp_set_params", "icarus_mlp_get_params", "icarus_mlp_features", "icarus_mlp_predict_leaves",
     "icarus_mlp_predict", "icarus_mlp_grad", "icarus_mlp_dataset_clear", "icarus_mlp_dataset_add",
-    "icarus_mlp_train", "icarus_destroy",
+    "icarus_mlp_train", "icarus_cell_updates", "icarus_destroy",
     "icarus_status_string",
 ]
 
@@ -275,6 +275,14 @@ class Icarus:
     def dt(self):
         out = np.zeros(self.n_members)
         _chk("icarus_get_dt", self.lib.icarus_get_dt(self.ctx, _dp(out)))
+        return out
+
+    def cell_updates(self):
+        out = np.zeros(self.n_members)
+        f = self.lib.icarus_cell_updates
+        f.restype = C.c_int
+        f.argtypes = [C.c_void_p, C.POINTER(C.c_double)]
+        _chk("icarus_cell_updates", f(self.ctx, _dp(out)))
         return out
 
     def status(self):

@@ -44,3 +44,42 @@ def test_earth_moves_at_the_synodic_rate():
     assert abs(p0[0] - 1.0) < 1e-15 and abs(p0[1] - math.pi / 2) < 1e-15
     # one synodic rotation later the longitude is back (27.2753 d)
     assert abs(((p1[2] - p0[2] + math.pi) % (2 * math.pi)) - math.pi) < 1e-3
+
+
+# ---------------------------------------------------------------- pre-flag bookkeeping
+def _tree(rows):
+    return np.array(rows, dtype=np.int32).reshape(-1, 4)
+
+
+def test_labels_follow_the_region_across_a_regrid():
+    # regrid k: two base leaves; between k and k+1 leaf 0 was refined
+    tk = _tree([[1, 0, 0, 0], [1, 1, 0, 0]])
+    children = [[2, (c >> 2) & 1, (c >> 1) & 1, c & 1] for c in range(8)]
+    tk1 = _tree(children + [[1, 1, 0, 0]])
+    # one child flagged at k+1 -> the parent region at k is labelled 1
+    f = np.zeros(9, dtype=np.int8)
+    f[3] = 1
+    assert H.next_regrid_labels(tk, tk1, f).tolist() == [1.0, 0.0]
+    # the unchanged leaf flagged at k+1 -> itself labelled
+    f = np.zeros(9, dtype=np.int8)
+    f[8] = 1
+    assert H.next_regrid_labels(tk, tk1, f).tolist() == [0.0, 1.0]
+    # coarsening flags (-1) are not refinements
+    assert H.next_regrid_labels(tk, tk1, -np.ones(9, dtype=np.int8)).tolist() == [0.0, 0.0]
+    # k+1 leaf coarser than the k leaves (8 children merged): all 8 labelled
+    assert H.next_regrid_labels(tk1, tk, np.array([1, 0], dtype=np.int8)).tolist() == [1.0] * 8 + [0.0]
+
+
+def test_missed_flag_rate_counts_unmarked_regions():
+    tk = _tree([[1, 0, 0, 0], [1, 1, 0, 0], [1, 2, 0, 0]])
+    tk1 = tk.copy()
+    f1 = np.array([1, 1, 0], dtype=np.int8)
+    assert H.missed_flag_rate(tk, np.array([True, False, False]), tk1, f1) == 0.5
+    assert H.missed_flag_rate(tk, np.array([True, True, True]), tk1, f1) == 0.0
+    assert H.missed_flag_rate(tk, np.array([False, False, True]), tk1, f1) == 1.0
+    assert H.missed_flag_rate(tk, np.zeros(3, bool), tk1, np.zeros(3, np.int8)) is None
+    # at the finest level a flag cannot act: excluded when max_level is given
+    tk2 = _tree([[2, 0, 0, 0], [1, 1, 0, 0]])
+    f2 = np.array([1, 1], dtype=np.int8)
+    assert H.missed_flag_rate(tk2, np.zeros(2, bool), tk2, f2) == 1.0
+    assert H.missed_flag_rate(tk2, np.array([False, True]), tk2, f2, max_level=2) == 0.0
