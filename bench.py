@@ -70,6 +70,7 @@ def parse():
     p.add_argument("--members", type=int, default=32)
     p.add_argument("--max-blocks", type=int, default=60000)
     p.add_argument("--train-regrids", type=int, default=60)
+    p.add_argument("--batch", type=int, default=8, help="tt1au: members of the batched learned arm")
     p.add_argument("--max-level", type=int, default=4)
     p.add_argument("--hours", type=float, default=72.0)
     p.add_argument("--relax-days", type=float, default=10.0)
@@ -257,7 +258,7 @@ def run_ensemble_workload(args):
     t_inj, wall_relax = WL.relax(g, args.relax_days)
     ups0 = float(np.sum(g.cell_updates()))
     res = WL.run_cme(g, draws, t_inj=t_inj, hours_after=args.hours, regrid_every=args.regrid_every,
-                     max_levels=[d["max_level"] for d in draws])
+                     max_levels=[d["max_level"] for d in draws], stop_hours_after_arrival=6.0)
     rep = WL.amr_report(g, res, wall_relax, t_inj, ups0)
     print(json.dumps({"workload": f"ensemble{args.members}_amr264x36x96", "precision": "fp32",
                       "hours_after_injection": args.hours, "max_levels": [d["max_level"] for d in draws], **rep}),
@@ -282,10 +283,9 @@ def run_tt1au_workload(args):
     g.inject_cone_cme(0, t_start=t_inj, **I.cme_config2(seed=7))
     # labels one regrid ahead at the interval the learned run uses
     recs = H.collect_regrids(g, n_regrids=args.train_regrids, regrid_every=2 * args.regrid_every, crit=WL.CRIT)
-    X, T = H.training_pairs(recs)
-    if len(T) > 65536:   # the device dataset holds 65536 pairs: seeded subsample
-        sel = np.sort(np.random.default_rng(2).choice(len(T), 65536, replace=False))
-        X, T = X[sel], T[sel]
+    X, T = H.training_pairs(recs, max_level=L)
+    pos_frac = float(T.mean())
+    X, T = H.rebalance(X, T, seed=2)
     g.mlp_set_params(I.mlp_init(5).astype(np.float32))
     g.mlp_dataset_clear()
     g.mlp_dataset_add(X, T)
@@ -295,25 +295,46 @@ def run_tt1au_workload(args):
     theta = g.mlp_get_params()
     del g
     out = {}
-    for name, prec, learned, every in (("fp32_learned", FP32_MIXED, True, 2 * args.regrid_every),
-                                       ("fp64_plain", FP64, False, args.regrid_every)):
-        g = WL.amr_grid(max_level=L, precision=prec, max_blocks=args.max_blocks)
+    B = args.batch
+    for name, prec, learned, every, nm in (("fp32_learned", FP32_MIXED, True, 2 * args.regrid_every, 1),
+                                           (f"fp32_learned_batch{B}", FP32_MIXED, True, 2 * args.regrid_every, B),
+                                           ("fp32_plain", FP32_MIXED, False, args.regrid_every, 1),
+                                           ("fp64_plain", FP64, False, args.regrid_every, 1)):
+        if nm < 2 and name.startswith("fp32_learned_batch"):
+            continue
+        g = WL.amr_grid(n_members=nm, max_level=L, precision=prec, max_blocks=max(args.max_blocks, 15000 * nm))
         if learned:
             g.mlp_set_params(theta)
         WL.start_wind(g)
         t_inj, wall_relax = WL.relax(g, args.relax_days)
         ups0 = float(np.sum(g.cell_updates()))
-        res = WL.run_cme(g, [I.cme_config2(seed=0)], t_inj=t_inj, hours_after=args.hours, regrid_every=every,
-                         learned=learned)
+        # a batch holds nm copies of the same CME run (the time per instance
+        # is the batch's wall clock / nm)
+        res = WL.run_cme(g, [I.cme_config2(seed=0)] * nm, t_inj=t_inj, hours_after=args.hours,
+                         regrid_every=every, learned=learned)
         rep = WL.amr_report(g, res, wall_relax, t_inj, ups0)
-        arr = res.arrival[0]
-        if arr is not None:   # wall clock to the arrival sample, by linear share of the run
-            rep["time_to_arrival_s"] = res.wall_s * (arr - t_inj) / (res.times[-1] - t_inj)
+        rep["members"] = nm
+        rep["time_to_arrival_s"] = res.wall_to(res.arrival[0])
+        if rep["time_to_arrival_s"] is not None:
+            rep["time_to_arrival_per_instance_s"] = rep["time_to_arrival_s"] / nm
+        rep["series_at_earth"] = {"t_h": ((res.times - t_inj) / I.hours(1.0)).tolist(),
+                                  "vr_kms": (res.series[0, :, 1] * 100.0).tolist(),
+                                  "n": res.series[0, :, 0].tolist()}
         out[name] = rep
+        print(json.dumps({"arm": name, **{k: v for k, v in rep.items() if k != "series_at_earth"}}), flush=True)
         del g
     a32, a64 = out["fp32_learned"]["arrival_h"][0], out["fp64_plain"]["arrival_h"][0]
+    # FP32 against FP64 along the Earth probe series (both plain flags)
+    s32, s64 = out["fp32_plain"]["series_at_earth"], out["fp64_plain"]["series_at_earth"]
+    serr = {}
+    for key in ("vr_kms", "n"):
+        x, y = np.asarray(s32[key]), np.asarray(s64[key])
+        serr[key + "_max_abs_diff"] = float(np.max(np.abs(x - y)))
+        serr[key + "_max_rel_diff"] = float(np.max(np.abs(x - y)) / np.max(np.abs(y)))
     print(json.dumps({"workload": f"tt1au_amr264x36x96_L{L}", "train_pairs": int(len(T)),
+                      "label_positive_fraction": pos_frac,
                       "train_loss": [float(losses[0]), float(losses[-1])], "train_s": train_s, **out,
+                      "fp32_vs_fp64_series": serr,
                       "arrival_diff_h": None if (a32 is None or a64 is None) else abs(a32 - a64)}), flush=True)
     return 0
 

@@ -120,8 +120,10 @@ typedef struct {
  * pressure (diagonal form, index space, noise parameter eps).  A block is
  * flagged +1 (refine) if some interior cell has E > e_refine and
  * v_r > v_r,background + dv; -1 (coarsen) if no cell has E > e_coarsen with
- * that gate; 0 otherwise.  mode: ICARUS_FLAG_PLAIN, _LEARNED (MLP
- * pre-flags OR plain flags), _BOTH (both computed, plain flags returned). */
+ * that gate; 0 otherwise.  mode: ICARUS_FLAG_PLAIN, _LEARNED (plain flags,
+ * set to +1 where the MLP pre-flagger's probability exceeds 1/2 on a block
+ * below its member's finest level), _BOTH (both computed, plain flags
+ * returned). */
 typedef struct {
   double e_refine, e_coarsen, eps, dv;
   int mode;

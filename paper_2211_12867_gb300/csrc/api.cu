@@ -385,6 +385,7 @@ icarus_status upload_tree(icarus_ctx *c, DevBlock *blk_dst) {
       DevBlock &B = c->hblk[slot];
       B.member = m;
       B.level = l.level;
+      B.lmax = M.max_level;
       for (int k = 0; k < 3; k++) B.ix[k] = l.ix[k];
       B.phys = 0;
       bool finer = false;
@@ -671,7 +672,10 @@ void default_tiles(icarus_ctx *c) {
     c->occ = stage_max_ctas_per_sm(c->prec, c->tile_j, c->tile_k);
     return;
   }
-  if (n2 >= 32) {
+  if (c->prec && n1 >= 12 && n2 >= 20) {
+    c->tile_j = 12;
+    c->tile_k = 20;
+  } else if (n2 >= 32) {
     c->tile_j = c->prec ? 8 : 4;
     c->tile_k = 32;
   } else if (n1 >= 12 && n2 >= 12) {
@@ -1049,6 +1053,13 @@ icarus_status icarus_set_time(icarus_ctx *c, int member, double t) {
 icarus_status icarus_set_member_max_level(icarus_ctx *c, int member, int L) {
   if (!member_ok(c, member) || L < 1 || L > c->d.max_level) return ICARUS_ERR_ARG;
   c->mem[member].max_level = L;
+  // the block table carries each block's finest level (learned pre-flags)
+  const int off = c->mem_off[member], n = (int)c->mem[member].leaves.size();
+  if (n > 0 && (int)c->hblk.size() >= off + n) {
+    for (int s = off; s < off + n; s++) c->hblk[s].lmax = L;
+    CK(cudaMemcpyAsync(c->blk + off, c->hblk.data() + off, sizeof(DevBlock) * n, cudaMemcpyHostToDevice, c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+  }
   return ICARUS_OK;
 }
 
@@ -1262,7 +1273,7 @@ icarus_status icarus_flag_refine(icarus_ctx *c, const icarus_refine *crit, int8_
   if (crit->mode == ICARUS_FLAG_LEARNED) {
     if (!c->mlp_ready) return ICARUS_ERR_STATE;
     mlp_leaf_probabilities(c);
-    mlp_combine_launch(c->mlp_prob, c->flags, c->nleaves, c->stream);
+    mlp_combine_launch(c->mlp_prob, c->blk, c->flags, c->nleaves, c->stream);
   }
   CK(cudaPeekAtLastError());
   c->hflags.assign(c->nleaves, 0);

@@ -21,7 +21,7 @@ struct DevBlock {
   int ix[3];
   int nbr[6];      // NB_* per face (dir*2 + side)
   int phys;        // bit (2*d+side): block touches a non-periodic boundary there
-  int pad;
+  int lmax;        // finest level of the block's member
 };
 
 // 1D geometry tables of one level, indexed with an offset of NGH so that the
@@ -160,7 +160,7 @@ void mlp_backward_launch(const float *theta, const float *X, const float *T, con
                          const float *h1, const float *h2, const float *y, float *dz, float *dh2, float *dh1,
                          float *grad, float *loss, cudaStream_t s);
 void mlp_adam_launch(float *theta, const float *g, float *m, float *v, float lr, int step, cudaStream_t s);
-void mlp_combine_launch(const float *prob, signed char *flags, int n, cudaStream_t s);
+void mlp_combine_launch(const float *prob, const DevBlock *blk, signed char *flags, int n, cudaStream_t s);
 
 struct icarus_ctx;
 int ctx_member_view(icarus_ctx *c, int member, KParams *kp, const void **U, int *precision, int *slot0,

@@ -208,9 +208,10 @@ __global__ void k_adam(float *theta, const float *g, float *m, float *v, int n, 
 }
 
 // combine: refine where the predictor says so, otherwise keep the plain flag
-__global__ void k_combine(const float *prob, signed char *flags, int n) {
+// learned pre-flag: probability above 1/2 on a block that can still refine
+__global__ void k_combine(const float *prob, const DevBlock *blk, signed char *flags, int n) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i < n && prob[i] > 0.5f) flags[i] = 1;
+  if (i < n && prob[i] > 0.5f && blk[i].level < blk[i].lmax) flags[i] = 1;
 }
 
 }  // namespace
@@ -248,6 +249,6 @@ void mlp_adam_launch(float *theta, const float *g, float *m, float *v, float lr,
   k_adam<<<(np + 255) / 256, 256, 0, s>>>(theta, g, m, v, np, lr, b1, b2, 1e-8f, bc1, bc2);
 }
 
-void mlp_combine_launch(const float *prob, signed char *flags, int n, cudaStream_t s) {
-  if (n > 0) k_combine<<<(n + 255) / 256, 256, 0, s>>>(prob, flags, n);
+void mlp_combine_launch(const float *prob, const DevBlock *blk, signed char *flags, int n, cudaStream_t s) {
+  if (n > 0) k_combine<<<(n + 255) / 256, 256, 0, s>>>(prob, blk, flags, n);
 }

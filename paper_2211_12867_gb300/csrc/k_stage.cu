@@ -33,22 +33,69 @@ namespace {
 template <typename real>
 struct StageSmem {
   static constexpr size_t bytes(int tj, int tk) {
-    return sizeof(real) * (size_t)(6 * NVAR * (tj + 4) * (tk + 4) + NVAR * (tj + 1) * tk +
-                                   NVAR * tj * (tk + 1) + 4 * (tj + 2) * (tk + 2));
+    return sizeof(real) * (size_t)(5 * NVAR * (tj + 4) * (tk + 4) + 2 * NVAR * (tj + 1) * tk +
+                                   2 * NVAR * tj * (tk + 1) + 4 * (tj + 2) * (tk + 2) +
+                                   NVAR * ((tj * tk + 31) / 32 * 32));
   }
 };
 
-__device__ __forceinline__ void flush_acc(const KParams &kp, double &acc, int member, long long &hits) {
+// The inverse time step is accumulated in the working precision (a maximum is
+// exact in any precision) and enters the FP64 reduction once per warp.
+template <typename real>
+__device__ __forceinline__ void flush_acc(const KParams &kp, real &acc, int member, long long &hits) {
   // warp max of the inverse time step, one atomic per warp
-  for (int o = 16; o > 0; o >>= 1) acc = fmax(acc, __shfl_xor_sync(0xffffffffu, acc, o));
+  for (int o = 16; o > 0; o >>= 1) acc = RT<real>::max_(acc, __shfl_xor_sync(0xffffffffu, acc, o));
   long long h = hits;
   for (int o = 16; o > 0; o >>= 1) h += __shfl_xor_sync(0xffffffffu, h, o);
   if ((threadIdx.x & 31) == 0 && member >= 0) {
-    if (acc > 0.0) atomic_max_pos(&kp.inv_max[member], acc);
+    if (acc > real(0)) atomic_max_pos(&kp.inv_max[member], (double)acc);
     if (h) atomicAdd(kp.floor_hits, (unsigned long long)h);
   }
-  acc = 0.0;
+  acc = real(0);
   hits = 0;
+}
+
+// Shared arrays of 8-variable cells (the primitive ring, the face fluxes) are
+// stored as [NVAR / CH][cell][CH] with CH = 16 bytes / sizeof(real): a cell's
+// variables come in NVAR / CH 16-byte loads and consecutive cells are
+// consecutive vectors (no bank conflicts between neighbouring threads).
+template <typename real> struct Vec16;
+template <> struct Vec16<float> {
+  using T = float4;
+  static constexpr int CH = 4;
+  static __device__ __forceinline__ void put(T x, float *w) { w[0] = x.x; w[1] = x.y; w[2] = x.z; w[3] = x.w; }
+  static __device__ __forceinline__ T get(const float *w) { return make_float4(w[0], w[1], w[2], w[3]); }
+};
+template <> struct Vec16<double> {
+  using T = double2;
+  static constexpr int CH = 2;
+  static __device__ __forceinline__ void put(T x, double *w) { w[0] = x.x; w[1] = x.y; }
+  static __device__ __forceinline__ T get(const double *w) { return make_double2(w[0], w[1]); }
+};
+template <typename real, int N>
+__device__ __forceinline__ void ld8(const real *a, int q, real *w) {
+  using V = Vec16<real>;
+#pragma unroll
+  for (int c = 0; c < NVAR / V::CH; c++)
+    V::put(*reinterpret_cast<const typename V::T *>(a + (c * N + q) * V::CH), w + c * V::CH);
+}
+template <typename real, int N>
+__device__ __forceinline__ void st8(real *a, int q, const real *w) {
+  using V = Vec16<real>;
+#pragma unroll
+  for (int c = 0; c < NVAR / V::CH; c++)
+    *reinterpret_cast<typename V::T *>(a + (c * N + q) * V::CH) = V::get(w + c * V::CH);
+}
+// one variable of a cell in that layout
+template <typename real, int N>
+__device__ __forceinline__ real &el(real *a, int v, int q) {
+  constexpr int CH = Vec16<real>::CH;
+  return a[((v / CH) * N + q) * CH + v % CH];
+}
+template <typename real, int N>
+__device__ __forceinline__ real el(const real *a, int v, int q) {
+  constexpr int CH = Vec16<real>::CH;
+  return a[((v / CH) * N + q) * CH + v % CH];
 }
 
 // threads per CTA: the tile's cells rounded up to whole warps (the extra
@@ -60,12 +107,13 @@ __global__ void __launch_bounds__(stage_threads(TJ, TK), (sizeof(real) == 4 ? 2 
     k_stage(const KParams kp, const StageLaunch sl) {
   constexpr int NT = stage_threads(TJ, TK), RJ = TJ + 4, RK = TK + 4, RP = RJ * RK;
   constexpr int DJ = TJ + 2, DK = TK + 2, DP = DJ * DK;
+  constexpr int NTH = (TJ + 1) * TK, NPH = TJ * (TK + 1);   // theta / phi faces of a plane
   extern __shared__ __align__(16) unsigned char smem_raw[];
   real *ring = reinterpret_cast<real *>(smem_raw);
-  real *stage = ring + 5 * NVAR * RP;   // raw conserved variables of the next plane
-  real *fth = stage + NVAR * RP;
-  real *fph = fth + NVAR * (TJ + 1) * TK;
-  real *dring = fph + NVAR * TJ * (TK + 1);
+  real *fth = ring + 5 * NVAR * RP;     // two buffers of theta-face fluxes
+  real *fph = fth + 2 * NVAR * NTH;     // two buffers of phi-face fluxes
+  real *dring = fph + 2 * NVAR * NPH;
+  real *u0s = dring + 4 * DP;           // U^n of the thread's own cell, next plane
 
   const int tid = threadIdx.x, jl = tid / TK, kl = tid % TK;
   const real gamma = (real)kp.gamma, pfl = (real)kp.p_floor, rfl = (real)kp.rho_floor;
@@ -84,7 +132,7 @@ __global__ void __launch_bounds__(stage_threads(TJ, TK), (sizeof(real) == 4 ? 2 
   const int fc0 = nb1 * nb2, fc1 = nb0 * nb2, fc2 = nb0 * nb1;
   const size_t fstride = (size_t)NVAR * 2 * (fc0 + fc1 + fc2);
 
-  double inv_acc = 0.0;
+  real inv_acc = real(0);
   long long hits = 0;
   int cur_member = -1;
 
@@ -114,54 +162,70 @@ __global__ void __launch_bounds__(stage_threads(TJ, TK), (sizeof(real) == 4 ? 2 
     const int j = j0 + jl, k = k0 + kl;           // interior indices in the block
     const int J = J0 + jl, K = K0 + kl;           // global indices at the level
 
-    // Planes are copied asynchronously (cp.async, 2 cells x 8 variables per
-    // unit) into the staging buffer one iteration ahead; the thread that
-    // copied a unit later converts it to primitives, so no barrier is needed
-    // between the copy and the conversion.
+    // Planes of U_in are copied asynchronously (cp.async, 2 cells x 8
+    // variables per unit) straight into their ring slot and converted to
+    // primitives in place one iteration later, by the thread that copied them
+    // (no barrier between copy and conversion).  Units go to the highest
+    // thread indices, which own no second div B position.
     constexpr int HK = RK / 2, NU = RJ * HK;
+    auto slotp = [&](int p) -> real * { return ring + ((p + 5) % 5) * NVAR * RP; };
     auto issue_plane = [&](int p) {
+      real *dst = slotp(p);
       const real *src = Uin + (size_t)(p + NGH) * plane;
-      for (int u = tid; u < NU; u += NT) {
+      for (int u = NT - 1 - tid; u < NU; u += NT) {
         const int jj = u / HK, kk = 2 * (u - (u / HK) * HK);
         const int pj = j0 + jj, pk = k0 + kk;
         if (pj < P1 && pk < P2) {
+          const int q = jj * RK + kk;
 #pragma unroll
-          for (int v = 0; v < NVAR; v++)
-            cp_async<2 * sizeof(real)>(stage + v * RP + jj * RK + kk, src + v * vstride + (size_t)pj * P2 + pk);
+          for (int v = 0; v < NVAR; v++) {
+            const real *g = src + v * vstride + (size_t)pj * P2 + pk;
+            cp_async<sizeof(real)>(&el<real, RP>(dst, v, q), g);
+            cp_async<sizeof(real)>(&el<real, RP>(dst, v, q + 1), g + 1);
+          }
         }
       }
       cp_async_commit();
     };
     auto convert_plane = [&](int p) {
-      cp_async_wait_all();
-      real *dst = ring + ((p + 5) % 5) * NVAR * RP;
-      for (int u = tid; u < NU; u += NT) {
+      real *pl = slotp(p);
+      for (int u = NT - 1 - tid; u < NU; u += NT) {
         const int jj = u / HK, kk = 2 * (u - (u / HK) * HK);
         if (j0 + jj < P1 && k0 + kk < P2) {
 #pragma unroll
           for (int h = 0; h < 2; h++) {
             const int q = jj * RK + kk + h;
             real uu[NVAR], wv[NVAR];
-#pragma unroll
-            for (int v = 0; v < NVAR; v++) uu[v] = stage[v * RP + q];
+            ld8<real, RP>(pl, q, uu);
             cons2prim<real>(uu, wv, gamma, pfl, isl);
-#pragma unroll
-            for (int v = 0; v < NVAR; v++) dst[v * RP + q] = wv[v];
+            st8<real, RP>(pl, q, wv);
           }
         }
       }
     };
-    auto ringp = [&](int p) -> const real * { return ring + ((p + 5) % 5) * NVAR * RP; };
-    auto gather = [&](const real *pl, int jj, int kk, real *w) {
+    // U^n of the thread's own cell at plane p, copied asynchronously one
+    // plane ahead (only this thread reads it: no barrier); always commits a
+    // group so that the group counts stay uniform
+    auto issue_u0 = [&](int p) {
+      if (valid && p < ie) {
+        const real *src = U0 + (size_t)(p + NGH) * plane + (size_t)(j + NGH) * P2 + (k + NGH);
 #pragma unroll
-      for (int v = 0; v < NVAR; v++) w[v] = pl[v * RP + jj * RK + kk];
+        for (int v = 0; v < NVAR; v++) cp_async<sizeof(real)>(u0s + v * NT + tid, src + v * vstride);
+      }
+      cp_async_commit();
     };
-    // limited radial slope at plane p of the thread's column
+    auto ringp = [&](int p) -> const real * { return ring + ((p + 5) % 5) * NVAR * RP; };
+    auto gather = [&](const real *pl, int jj, int kk, real *w) { ld8<real, RP>(pl, jj * RK + kk, w); };
+    // half the limited radial slope at plane p of the thread's column
     auto rslope = [&](int p, real *sl_) {
       const real *pm = ringp(p - 1), *pc = ringp(p), *pp = ringp(p + 1);
       const int o = (jl + 2) * RK + kl + 2;
+      real a[NVAR], b[NVAR], c[NVAR];
+      ld8<real, RP>(pm, o, a);
+      ld8<real, RP>(pc, o, b);
+      ld8<real, RP>(pp, o, c);
 #pragma unroll
-      for (int v = 0; v < NVAR; v++) sl_[v] = mc_slope<real>(pm[v * RP + o], pc[v * RP + o], pp[v * RP + o]);
+      for (int v = 0; v < NVAR; v++) sl_[v] = mc_half_slope<real>(a[v], b[v], c[v]);
     };
     // radial face between planes p-1 and p from the slopes at both planes
     auto rflux = [&](int p, const real *sm, const real *sp, real *F) {
@@ -170,8 +234,8 @@ __global__ void __launch_bounds__(stage_threads(TJ, TK), (sizeof(real) == 4 ? 2 
       gather(ringp(p), jl + 2, kl + 2, c);
 #pragma unroll
       for (int v = 0; v < NVAR; v++) {
-        WL[v] = b[v] + real(0.5) * sm[v];
-        WR[v] = c[v] - real(0.5) * sp[v];
+        WL[v] = b[v] + sm[v];
+        WR[v] = c[v] - sp[v];
       }
       tvdlf_states<real, 0>(WL, WR, b, c, gamma, igm1, F);
     };
@@ -189,9 +253,10 @@ __global__ void __launch_bounds__(stage_threads(TJ, TK), (sizeof(real) == 4 ? 2 
         if (dj > nvj || dk > nvk) continue;
         const int jj = dj + 2, kk = dk + 2;
         const int Jg = J0 + dj, Kg = K0 + dk;
-        const real brm = pm[5 * RP + jj * RK + kk], brp = pp[5 * RP + jj * RK + kk];
-        const real btm = pc[6 * RP + (jj - 1) * RK + kk], btp = pc[6 * RP + (jj + 1) * RK + kk];
-        const real bpm = pc[7 * RP + jj * RK + kk - 1], bpp = pc[7 * RP + jj * RK + kk + 1];
+        const int o = jj * RK + kk;
+        const real brm = el<real, RP>(pm, 5, o), brp = el<real, RP>(pp, 5, o);
+        const real btm = el<real, RP>(pc, 6, o - RK), btp = el<real, RP>(pc, 6, o + RK);
+        const real bpm = el<real, RP>(pc, 7, o - 1), bpp = el<real, RP>(pc, 7, o + 1);
         const real tcm = G.tc[Jg - 1 + NGH], tcp = G.tc[Jg + 1 + NGH];
         const real pcm = G.pc[Kg - 1 + NGH], pcp = G.pc[Kg + 1 + NGH];
         real div;
@@ -208,12 +273,10 @@ __global__ void __launch_bounds__(stage_threads(TJ, TK), (sizeof(real) == 4 ? 2 
       }
     };
 
-    // ---- prologue: planes ib-2 .. ib+2 converted, ib+3 in flight ----
-    for (int p = ib - 2; p <= ib + 2; p++) {
-      issue_plane(p);
-      convert_plane(p);
-    }
-    if (ib + 3 <= ie + 1) issue_plane(ib + 3);
+    // ---- prologue: planes ib-2 .. ib+2 converted, r flux at face ib ----
+    for (int p = ib - 2; p <= ib + 2; p++) issue_plane(p);
+    cp_async_wait_all();
+    for (int p = ib - 2; p <= ib + 2; p++) convert_plane(p);
     __syncthreads();
     if (S2) {
       divb_plane(ib - 1);
@@ -226,22 +289,23 @@ __global__ void __launch_bounds__(stage_threads(TJ, TK), (sizeof(real) == 4 ? 2 
       rslope(ib, sc);
       rflux(ib, s0, sc, Flo);
     }
+    __syncthreads();   // plane ib-2 is read no more: its slot takes plane ib+3
+    if (ib + 3 <= ie + 1) issue_plane(ib + 3);
+    else cp_async_commit();
+    issue_u0(ib);
 
+    // One barrier per plane.  Phase A (before it): theta and phi face fluxes
+    // of plane i into face buffer i&1, div B of plane i+1, conversion of plane
+    // i+3.  Phase B (after it): r flux at face i+1 and the update of the
+    // thread's cell of plane i, then the copies of plane i+4 (into the slot of
+    // plane i-1, which neither phase reads any more) and of U^n at plane i+1.
+    // A thread in phase A of plane i+1 can overlap others still in phase B of
+    // plane i: they use the other face buffer, another div B slot and
+    // disjoint ring slots.
     for (int i = ib; i < ie; i++) {
-      if (i > ib) __syncthreads();   // plane i+2 converted by every thread
-      if (S2) divb_plane(i + 1);
-      real Fhi[NVAR];
-      if (valid) {
-        real sn[NVAR];
-        rslope(i + 1, sn);
-        rflux(i + 1, sc, sn, Fhi);
-#pragma unroll
-        for (int v = 0; v < NVAR; v++) sc[v] = sn[v];
-      }
-      // theta and phi faces of plane i
+      real *fthb = fth + (i & 1) * NVAR * NTH, *fphb = fph + (i & 1) * NVAR * NPH;
       {
         const real *pl = ringp(i);
-        constexpr int NTH = (TJ + 1) * TK, NPH = TJ * (TK + 1);
         for (int f = tid; f < NTH + NPH; f += NT) {
           real a[NVAR], b[NVAR], c[NVAR], e[NVAR], F[NVAR];
           if (f < NTH) {
@@ -252,8 +316,7 @@ __global__ void __launch_bounds__(stage_threads(TJ, TK), (sizeof(real) == 4 ? 2 
               gather(pl, row + 2, col + 2, c);
               gather(pl, row + 3, col + 2, e);
               tvdlf_face<real, 1>(a, b, c, e, gamma, igm1, F);
-#pragma unroll
-              for (int v = 0; v < NVAR; v++) fth[(v * (TJ + 1) + row) * TK + col] = F[v];
+              st8<real, NTH>(fthb, row * TK + col, F);
             }
           } else {
             const int g = f - NTH, row = g / (TK + 1), col = g - (g / (TK + 1)) * (TK + 1);
@@ -263,13 +326,25 @@ __global__ void __launch_bounds__(stage_threads(TJ, TK), (sizeof(real) == 4 ? 2 
               gather(pl, row + 2, col + 2, c);
               gather(pl, row + 2, col + 3, e);
               tvdlf_face<real, 2>(a, b, c, e, gamma, igm1, F);
-#pragma unroll
-              for (int v = 0; v < NVAR; v++) fph[(v * TJ + row) * (TK + 1) + col] = F[v];
+              st8<real, NPH>(fphb, row * (TK + 1) + col, F);
             }
           }
         }
       }
+      if (S2) divb_plane(i + 1);
+      if (i + 3 <= ie + 1) {
+        cp_async_wait_group<1>();   // plane i+3 landed (U^n of plane i may not have)
+        convert_plane(i + 3);
+      }
       __syncthreads();
+      real Fhi[NVAR];
+      if (valid) {
+        real sn[NVAR];
+        rslope(i + 1, sn);
+        rflux(i + 1, sc, sn, Fhi);
+#pragma unroll
+        for (int v = 0; v < NVAR; v++) sc[v] = sn[v];
+      }
       if (valid) {
         const int I = I0 + i;
         const int iI = I + NGH, iJ = J + NGH;
@@ -284,12 +359,24 @@ __global__ void __launch_bounds__(stage_threads(TJ, TK), (sizeof(real) == 4 ? 2 
         gather(ringp(i), jl + 2, kl + 2, w);
         real un[NVAR];
         const size_t cidx = (size_t)(i + NGH) * plane + (size_t)(j + NGH) * P2 + (k + NGH);
+        {
+          constexpr int CH = Vec16<real>::CH;
+          const int qt = jl * TK + kl, qp = jl * (TK + 1) + kl;
 #pragma unroll
-        for (int v = 0; v < NVAR; v++) {
-          const real ftl = fth[(v * (TJ + 1) + jl) * TK + kl], fth_ = fth[(v * (TJ + 1) + jl + 1) * TK + kl];
-          const real fpl = fph[(v * TJ + jl) * (TK + 1) + kl], fph_ = fph[(v * TJ + jl) * (TK + 1) + kl + 1];
-          const real div = (Arp * Fhi[v] - Arm * Flo[v]) + (Atp * fth_ - Atm * ftl) + Ap * (fph_ - fpl);
-          un[v] = -div * iV;
+          for (int c = 0; c < NVAR / CH; c++) {
+            real ftl[CH], fth_[CH], fpl[CH], fph_[CH];
+            using V = Vec16<real>;
+            V::put(*reinterpret_cast<const typename V::T *>(fthb + (c * NTH + qt) * CH), ftl);
+            V::put(*reinterpret_cast<const typename V::T *>(fthb + (c * NTH + qt + TK) * CH), fth_);
+            V::put(*reinterpret_cast<const typename V::T *>(fphb + (c * NPH + qp) * CH), fpl);
+            V::put(*reinterpret_cast<const typename V::T *>(fphb + (c * NPH + qp + 1) * CH), fph_);
+#pragma unroll
+            for (int h = 0; h < CH; h++) {
+              const int v = c * CH + h;
+              const real div = (Arp * Fhi[v] - Arm * Flo[v]) + (Atp * fth_[h] - Atm * ftl[h]) + Ap * (fph_[h] - fpl[h]);
+              un[v] = -div * iV;
+            }
+          }
         }
         if (spherical) {
           const real gr = (Arp - Arm) * iV, gt = (Atp - Atm) * iV, ir = real(0.5) * gr;
@@ -308,7 +395,9 @@ __global__ void __launch_bounds__(stage_threads(TJ, TK), (sizeof(real) == 4 ? 2 
           un[4] += rho * Om * Om * rc * st * vs;
         }
 #pragma unroll
-        for (int v = 0; v < NVAR; v++) un[v] = U0[v * vstride + cidx] + dt * un[v];
+        cp_async_wait_group<0>();   // this thread's U^n copy of plane i
+#pragma unroll
+        for (int v = 0; v < NVAR; v++) un[v] = u0s[v * NT + tid] + dt * un[v];
         if (S2 && Cd > real(0)) {
           const real *dm = dring + ((i - 1) & 3) * DP, *dc = dring + (i & 3) * DP, *dp = dring + ((i + 1) & 3) * DP;
           const int q = (jl + 1) * DK + (kl + 1);
@@ -360,7 +449,7 @@ __global__ void __launch_bounds__(stage_threads(TJ, TK), (sizeof(real) == 4 ? 2 
             const real s = (RT<real>::abs_(wn[1]) + fast_speed<real, 0>(wn, gamma)) * RT<real>::rcp_(dx0) +
                            (RT<real>::abs_(wn[2]) + fast_speed<real, 1>(wn, gamma)) * RT<real>::rcp_(dx1) +
                            (RT<real>::abs_(wn[3]) + fast_speed<real, 2>(wn, gamma)) * RT<real>::rcp_(dx2);
-            inv_acc = fmax(inv_acc, (double)s);
+            inv_acc = RT<real>::max_(inv_acc, s);
           }
           if (sl.flux) {
             real *fb = reinterpret_cast<real *>(sl.flux) + (size_t)slot * fstride;
@@ -375,27 +464,27 @@ __global__ void __launch_bounds__(stage_threads(TJ, TK), (sizeof(real) == 4 ? 2 
             if (j == 0 && (B.nbr[2] == NB_COARSER || B.nbr[2] == NB_FINER))
 #pragma unroll
               for (int v = 0; v < NVAR; v++)
-                fb[o2 + (size_t)v * fc1 + i * nb2 + k] = Atm * fth[(v * (TJ + 1) + jl) * TK + kl];
+                fb[o2 + (size_t)v * fc1 + i * nb2 + k] = Atm * el<real, NTH>(fthb, v, jl * TK + kl);
             if (j == nb1 - 1 && (B.nbr[3] == NB_COARSER || B.nbr[3] == NB_FINER))
 #pragma unroll
               for (int v = 0; v < NVAR; v++)
-                fb[o2 + (size_t)NVAR * fc1 + (size_t)v * fc1 + i * nb2 + k] = Atp * fth[(v * (TJ + 1) + jl + 1) * TK + kl];
+                fb[o2 + (size_t)NVAR * fc1 + (size_t)v * fc1 + i * nb2 + k] = Atp * el<real, NTH>(fthb, v, (jl + 1) * TK + kl);
             if (k == 0 && (B.nbr[4] == NB_COARSER || B.nbr[4] == NB_FINER))
 #pragma unroll
               for (int v = 0; v < NVAR; v++)
-                fb[o4 + (size_t)v * fc2 + i * nb1 + j] = Ap * fph[(v * TJ + jl) * (TK + 1) + kl];
+                fb[o4 + (size_t)v * fc2 + i * nb1 + j] = Ap * el<real, NPH>(fphb, v, jl * (TK + 1) + kl);
             if (k == nb2 - 1 && (B.nbr[5] == NB_COARSER || B.nbr[5] == NB_FINER))
 #pragma unroll
               for (int v = 0; v < NVAR; v++)
-                fb[o4 + (size_t)NVAR * fc2 + (size_t)v * fc2 + i * nb1 + j] = Ap * fph[(v * TJ + jl) * (TK + 1) + kl + 1];
+                fb[o4 + (size_t)NVAR * fc2 + (size_t)v * fc2 + i * nb1 + j] = Ap * el<real, NPH>(fphb, v, jl * (TK + 1) + kl + 1);
           }
         }
 #pragma unroll
         for (int v = 0; v < NVAR; v++) Flo[v] = Fhi[v];
       }
-      // next plane: convert the one in flight, start the copy of the one after
-      if (i + 3 <= ie + 1) convert_plane(i + 3);
       if (i + 4 <= ie + 1) issue_plane(i + 4);
+      else cp_async_commit();
+      issue_u0(i + 1);
     }
     cp_async_wait_all();
     __syncthreads();  // shared memory is reused by the next work item
@@ -459,14 +548,20 @@ int occupancy(int tj, int tk) {
 
 }  // namespace
 
-int stage_tile_supported(int precision, int tj, int tk) {
-  (void)precision;
-  return (tj == 8 && tk == 8) || (tj == 12 && tk == 12) || (tj == 8 && tk == 32) || (tj == 4 && tk == 32) ||
-         (tj == 12 && tk == 20) || (tj == 6 && tk == 36);
-}
-
 size_t stage_smem_bytes(int precision, int tj, int tk) {
   return precision ? StageSmem<float>::bytes(tj, tk) : StageSmem<double>::bytes(tj, tk);
+}
+
+// an instantiated tile whose shared memory fits one CTA on this device
+int stage_tile_supported(int precision, int tj, int tk) {
+  const bool known = (tj == 8 && tk == 8) || (tj == 12 && tk == 12) || (tj == 8 && tk == 32) ||
+                     (tj == 4 && tk == 32) || (tj == 12 && tk == 20) || (tj == 6 && tk == 36);
+  if (!known) return 0;
+  int dev = 0, lim = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess ||
+      cudaDeviceGetAttribute(&lim, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess)
+    return 0;
+  return stage_smem_bytes(precision, tj, tk) <= (size_t)lim;
 }
 
 int stage_max_ctas_per_sm(int precision, int tj, int tk) {

@@ -18,12 +18,24 @@ template <> struct RT<double> {
   static __device__ __forceinline__ double max_(double a, double b) { return fmax(a, b); }
   static __device__ __forceinline__ double rcp_(double x) { return __drcp_rn(x); }
 };
+// FP32 mode: reciprocal and square root are the hardware approximations
+// (PTX rcp.approx / sqrt.approx, relative error within about 1 ulp); the
+// FP32 stencil is an approximation of the FP64 one at the 1e-6 level anyway
+// and the correctly rounded forms cost several dependent instructions each.
 template <> struct RT<float> {
-  static __device__ __forceinline__ float sqrt_(float x) { return sqrtf(x); }
+  static __device__ __forceinline__ float sqrt_(float x) {
+    float y;
+    asm("sqrt.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+  }
   static __device__ __forceinline__ float abs_(float x) { return fabsf(x); }
   static __device__ __forceinline__ float min_(float a, float b) { return fminf(a, b); }
   static __device__ __forceinline__ float max_(float a, float b) { return fmaxf(a, b); }
-  static __device__ __forceinline__ float rcp_(float x) { return __frcp_rn(x); }
+  static __device__ __forceinline__ float rcp_(float x) {
+    float y;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+  }
 };
 
 // Pressure from conserved variables.  In the mixed-precision mode the FP32
@@ -143,6 +155,18 @@ __device__ __forceinline__ real fast_speed(const real *w, real gamma) {
   return RT<real>::sqrt_(real(0.5) * (s + RT<real>::sqrt_(disc)));
 }
 
+// Half the monotonised-central slope: min(|dm|, |dm + dp| / 4, |dp|) with the
+// common sign, 0 at an extremum.  Equal, bit for bit, to 0.5 * mc_slope (the
+// factors are powers of two), with two multiplications fewer.
+template <typename real>
+__device__ __forceinline__ real mc_half_slope(real um, real u0, real up) {
+  real dm = u0 - um, dp = up - u0;
+  real s = dm + dp;
+  real lim = RT<real>::min_(RT<real>::min_(RT<real>::abs_(dm), RT<real>::abs_(dp)), real(0.25) * RT<real>::abs_(s));
+  lim = s > real(0) ? lim : -lim;
+  return dm * dp > real(0) ? lim : real(0);
+}
+
 template <typename real>
 __device__ __forceinline__ real mc_slope(real um, real u0, real up) {
   real dm = u0 - um, dp = up - u0;
@@ -206,8 +230,8 @@ __device__ __forceinline__ void tvdlf_face(const real *a, const real *b, const r
   real WL[NVAR], WR[NVAR];
 #pragma unroll
   for (int v = 0; v < NVAR; v++) {
-    WL[v] = b[v] + real(0.5) * mc_slope<real>(a[v], b[v], c[v]);
-    WR[v] = c[v] - real(0.5) * mc_slope<real>(b[v], c[v], e[v]);
+    WL[v] = b[v] + mc_half_slope<real>(a[v], b[v], c[v]);
+    WR[v] = c[v] - mc_half_slope<real>(b[v], c[v], e[v]);
   }
   tvdlf_states<real, D>(WL, WR, b, c, gamma, igm1, F);
 }
@@ -218,8 +242,15 @@ __device__ __forceinline__ void cp_async(void *smem, const void *gmem) {
   const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
   if (BYTES == 16)
     asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(s), "l"(gmem) : "memory");
-  else
+  else if (BYTES == 8)
     asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(s), "l"(gmem) : "memory");
+  else
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(s), "l"(gmem) : "memory");
+}
+// wait until at most N of this thread's most recent copy groups are pending
+template <int N>
+__device__ __forceinline__ void cp_async_wait_group() {
+  asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
 }
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
 __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;\n" ::: "memory"); }

@@ -82,12 +82,13 @@ def _related(tree_a, tree_b):
     return out
 
 
-def next_regrid_labels(tree_k, tree_k1, flags_k1):
+def next_regrid_labels(tree_k, tree_k1, flags_k1, max_level=None):
     """Label of each leaf at regrid k: 1 if the plain estimator flags any
-    overlapping leaf for refinement at regrid k+1."""
+    overlapping leaf for refinement at regrid k+1 (with `max_level`, only
+    flagged leaves that can still refine count)."""
     lab = np.zeros(len(tree_k), dtype=np.float32)
-    for hits, f in zip(_related(tree_k, tree_k1), flags_k1):
-        if f > 0:
+    for (l, _, _, _), hits, f in zip(tree_k1, _related(tree_k, tree_k1), flags_k1):
+        if f > 0 and (max_level is None or l < max_level):
             lab[hits] = 1.0
     return lab
 
@@ -121,13 +122,36 @@ def collect_regrids(g, n_regrids, regrid_every, t_stop=np.inf, crit=None):
     return recs
 
 
-def training_pairs(recs):
-    """(features at regrid k, label from the plain flags at regrid k+1)"""
+def training_pairs(recs, max_level=None):
+    """(features at regrid k, label from the plain flags at regrid k+1).
+    With `max_level`, leaves already at the finest level (whose flags a
+    regrid ignores) are left out and only refinable flags make labels."""
     X, T = [], []
     for a, b in zip(recs[:-1], recs[1:]):
-        X.append(a["feat"])
-        T.append(next_regrid_labels(a["tree"], b["tree"], b["flags"]))
+        lab = next_regrid_labels(a["tree"], b["tree"], b["flags"], max_level)
+        keep = np.ones(len(lab), bool) if max_level is None else np.asarray(a["tree"])[:, 0] < max_level
+        X.append(a["feat"][keep])
+        T.append(lab[keep])
     return np.concatenate(X), np.concatenate(T)
+
+
+def rebalance(X, T, cap=65536, seed=0):
+    """Training set with the positives repeated until they are about as many
+    as the negatives (refinement labels are rare, and a network trained on
+    the raw prior never reaches probability 1/2); at most `cap` samples, a
+    seeded subsample of the negatives if needed."""
+    rng = np.random.default_rng(seed)
+    pos, neg = np.nonzero(T > 0.5)[0], np.nonzero(T <= 0.5)[0]
+    if len(pos) == 0 or len(neg) == 0:
+        sel = np.arange(len(T))
+    else:
+        n_neg = min(len(neg), cap // 2)
+        neg = np.sort(rng.choice(neg, n_neg, replace=False))
+        pos = np.resize(pos, min(n_neg, cap - n_neg))   # repeated in order
+        sel = np.concatenate([neg, pos])
+        sel = sel[rng.permutation(len(sel))]
+    sel = sel[:cap]
+    return X[sel], T[sel]
 
 
 # ---------------------------------------------------------------- driver
@@ -143,12 +167,18 @@ class RunResult:
     regrids: int = 0
     leaves: list = field(default_factory=list)   # leaves per regrid (all members)
     wall_s: float = 0.0
+    wall_at: np.ndarray = None  # wall clock [s] since injection at each sample
+
+    def wall_to(self, t):
+        """Wall clock from injection until simulated time t (interpolated
+        between samples); None if t is None."""
+        return None if t is None else float(np.interp(t, self.times, self.wall_at))
 
 
 def advance_to(g, t_target, max_steps=1_000_000, regrid_every=0, crit=None, counters=None,
                on_regrid=None):
-    """Step every member until it reaches t_target (regridding every
-    `regrid_every` steps when > 0)."""
+    """Step every member until it reaches t_target (scalar or per member;
+    regridding every `regrid_every` steps when > 0)."""
     counters = counters if counters is not None else {"steps": 0, "regrids": 0, "leaves": []}
     counters.setdefault("since", 0)
     cells_per_block = int(np.prod(g.block))
@@ -173,14 +203,17 @@ def advance_to(g, t_target, max_steps=1_000_000, regrid_every=0, crit=None, coun
             counters["since"] = 0
             counters["regrids"] += 1
             counters["leaves"].append(g.n_leaves(-1))
-        if np.all(t >= t_target) or n >= max_steps or taken == 0:
+        if np.all(t >= np.asarray(t_target)) or n >= max_steps or taken == 0:
             return t
 
 
 def propagate(g, cmes, *, t_inj, duration, sample=None, earth_lon0=math.pi, regrid_every=0, crit=None,
-              on_regrid=None):
+              on_regrid=None, stop_after_arrival=None):
     """Inject one cone CME per member at t_inj and record Earth time series
-    every `sample` (default 10 min) for `duration`; returns RunResult."""
+    every `sample` (default 10 min) for `duration`; returns RunResult.  With
+    `stop_after_arrival` (code time), a member stops advancing once its shock
+    has arrived and that much time has passed (its later samples repeat the
+    last state)."""
     import time as _time
     sample = I.hours(1.0 / 6.0) if sample is None else sample
     nm = g.n_members
@@ -194,14 +227,22 @@ def propagate(g, cmes, *, t_inj, duration, sample=None, earth_lon0=math.pi, regr
     for m in range(nm):
         series[m, 0] = g.probe(m, pts[:1])[0]
     counters = {"steps": 0, "regrids": 0, "leaves": []}
+    wall_at = np.zeros(len(times))
     w0 = _time.perf_counter()
+    t_hold = np.full(nm, np.inf)   # time a member stopped at
     for k in range(1, len(times)):
-        advance_to(g, times[k], regrid_every=regrid_every, crit=crit, counters=counters, on_regrid=on_regrid)
+        target = np.minimum(times[k], t_hold)
+        advance_to(g, target, regrid_every=regrid_every, crit=crit, counters=counters, on_regrid=on_regrid)
         for m in range(nm):
             series[m, k] = g.probe(m, pts[k:k + 1])[0]
-    wall = _time.perf_counter() - w0
+            if stop_after_arrival is not None and not np.isfinite(t_hold[m]):
+                a = arrival_time(times[:k + 1], series[m, :k + 1, 1], bg[m, :k + 1, 1])
+                if a is not None and times[k] >= a + stop_after_arrival:
+                    t_hold[m] = times[k]
+        wall_at[k] = _time.perf_counter() - w0
+    wall = wall_at[-1]
     arr = [arrival_time(times, series[m, :, 1], bg[m, :, 1]) for m in range(nm)]
     wid = [shock_width(times, series[m, :, 1], a) for m, a in zip(range(nm), arr)]
     pk = [peak_speed(times, series[m, :, 1], a) for m, a in zip(range(nm), arr)]
     return RunResult(times, series, bg, arr, wid, pk, counters["steps"], counters["regrids"],
-                     counters["leaves"], wall)
+                     counters["leaves"], wall, wall_at)

@@ -74,10 +74,11 @@ def amr_report(g, res, wall_relax, t_inj, ups0=0.0):
 
 
 def run_cme(g, cmes, *, t_inj, hours_after=72.0, regrid_every=10, max_levels=None, learned=False,
-            sample_min=10.0):
+            sample_min=10.0, stop_hours_after_arrival=None):
     """Inject one CME per member at t_inj and propagate for `hours_after`
     with regrids every `regrid_every` steps and Earth probes every
-    `sample_min` minutes.  Returns the harness RunResult."""
+    `sample_min` minutes (a member stops `stop_hours_after_arrival` after its
+    shock arrival when given).  Returns the harness RunResult."""
     if max_levels is not None:
         for m, L in enumerate(max_levels):
             g.set_member_max_level(m, int(L))
@@ -85,5 +86,6 @@ def run_cme(g, cmes, *, t_inj, hours_after=72.0, regrid_every=10, max_levels=Non
     if learned:
         from .icarus import FLAG_LEARNED
         crit["mode"] = FLAG_LEARNED
+    stop = None if stop_hours_after_arrival is None else I.hours(stop_hours_after_arrival)
     return H.propagate(g, cmes, t_inj=t_inj, duration=I.hours(hours_after), sample=I.hours(sample_min / 60.0),
-                       regrid_every=regrid_every, crit=crit)
+                       regrid_every=regrid_every, crit=crit, stop_after_arrival=stop)

@@ -77,3 +77,35 @@ def test_training_separates_a_seeded_problem():
     assert losses[-1] < 0.5 * losses[0]
     acc = ((g.mlp_predict(X[3200:]) > 0.5) == (T[3200:] > 0.5)).mean()
     assert acc > 0.9, acc
+
+
+def test_learned_mode_flags_refinable_blocks_only():
+    """flag_refine in the learned mode = the plain flags, set to +1 where the
+    network's probability exceeds 1/2 on a block below its member's finest
+    level (same kernels, so the decision is bit-exact)."""
+    from paper_2211_12867_gb300.icarus import FLAG_LEARNED, FLAG_PLAIN
+    g, o = make_pair(n=(48, 24, 48), nb=(12, 12, 12), max_level=3, max_blocks=4000, **STR)
+    wind_setup(g, o)
+    # records the background speed the criterion's gate needs; the CME itself
+    # starts long after this test ends
+    g.inject_cone_cme(0, t_start=100.0, **I.cme_config2(seed=0))
+    g.step(10)
+    crit = dict(e_refine=0.02, e_coarsen=0.005, eps=0.01, dv=-1e9)
+    g.flag_refine(**crit, mode=FLAG_PLAIN)
+    g.regrid()
+    tree = g.tree(0)
+    assert tree[:, 0].max() == 2, "the test wants refined leaves"
+    # a network whose probabilities straddle 1/2 over these blocks
+    th = I.mlp_init(4).astype(np.float32)
+    g.mlp_set_params(th)
+    p = g.mlp_predict_leaves()
+    th[-1] -= np.float32(np.log(np.median(p) / (1 - np.median(p))))   # centre the output bias
+    g.mlp_set_params(th)
+    prob = g.mlp_predict_leaves()
+    assert 0 < (prob > 0.5).sum() < len(prob)
+    plain = g.flag_refine(**crit, mode=FLAG_PLAIN)
+    for lmax in (3, 2):
+        g.set_member_max_level(0, lmax)
+        learned = g.flag_refine(**crit, mode=FLAG_LEARNED)
+        want = np.where((prob > 0.5) & (tree[:, 0] < lmax), 1, plain)
+        assert np.array_equal(learned, want), lmax

@@ -60,7 +60,7 @@ def test_ragged_tiles_and_segments():
     """blocks that the (theta, phi) tile and the radial segment do not divide"""
     g, o = make_pair(n=(40, 20, 24), nb=(20, 10, 12))
     wind_setup(g, o)
-    for tile, seg in (((8, 8), 6), ((4, 32), 7), ((12, 12), 0), ((8, 32), 3)):
+    for tile, seg in (((8, 8), 6), ((4, 32), 7), ((12, 12), 0), ((6, 36), 3), ((12, 20), 5)):
         g2, o2 = make_pair(n=(40, 20, 24), nb=(20, 10, 12))
         wind_setup(g2, o2)
         g2.set_tile(*tile, seg)
@@ -68,6 +68,10 @@ def test_ragged_tiles_and_segments():
         o2.advance(3)
         err = rel_linf(g2.get_state(0), o2.get_state())
         assert err.max() < 1e-12, (tile, seg, err)
+    # an FP64 8 x 32 tile needs more shared memory than one CTA may have
+    from paper_2211_12867_gb300.icarus import IcarusError
+    with pytest.raises(IcarusError):
+        g.set_tile(8, 32, 0)
 
 
 def test_graph_and_direct_launch_agree():

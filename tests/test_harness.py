@@ -83,3 +83,26 @@ def test_missed_flag_rate_counts_unmarked_regions():
     f2 = np.array([1, 1], dtype=np.int8)
     assert H.missed_flag_rate(tk2, np.zeros(2, bool), tk2, f2) == 1.0
     assert H.missed_flag_rate(tk2, np.array([False, True]), tk2, f2, max_level=2) == 0.0
+
+
+def test_training_pairs_skip_the_finest_level():
+    tk = _tree([[2, 0, 0, 0], [1, 1, 0, 0]])
+    f1 = np.array([1, 1], dtype=np.int8)
+    recs = [{"tree": tk, "feat": np.arange(128, dtype=np.float32).reshape(2, 64), "flags": f1},
+            {"tree": tk, "feat": np.zeros((2, 64), np.float32), "flags": f1}]
+    X, T = H.training_pairs(recs)
+    assert T.tolist() == [1.0, 1.0] and X.shape == (2, 64)
+    X, T = H.training_pairs(recs, max_level=2)
+    # the level-2 leaf is dropped; the level-1 leaf keeps its refinable label
+    assert T.tolist() == [1.0] and X[0, 0] == 64.0
+
+
+def test_rebalance_repeats_rare_positives():
+    X = np.arange(1000, dtype=np.float32).reshape(1000, 1)
+    T = np.zeros(1000, np.float32)
+    T[[3, 500, 900]] = 1.0
+    Xb, Tb = H.rebalance(X, T, cap=600)
+    assert len(Tb) == 600 and Tb.sum() == 300
+    # every sample is an original pair, positives stay positive
+    assert np.all(T[Xb[:, 0].astype(int)] == Tb)
+    assert set(Xb[Tb > 0, 0].astype(int)) == {3, 500, 900}
