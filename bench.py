@@ -71,6 +71,8 @@ def parse():
     p.add_argument("--max-blocks", type=int, default=60000)
     p.add_argument("--train-regrids", type=int, default=60)
     p.add_argument("--batch", type=int, default=8, help="tt1au: members of the batched learned arm")
+    p.add_argument("--arms", default="fp32_learned,fp32_plain,fp64_plain",
+                   help="tt1au arms (fp32_learned, fp32_learned_batch, fp32_plain, fp64_plain)")
     p.add_argument("--max-level", type=int, default=4)
     p.add_argument("--hours", type=float, default=72.0)
     p.add_argument("--relax-days", type=float, default=10.0)
@@ -240,6 +242,7 @@ def run_amr_workload(args):
     ups0 = float(np.sum(g.cell_updates()))
     res = WL.run_cme(g, [cme], t_inj=t_inj, hours_after=args.hours, regrid_every=args.regrid_every)
     rep = WL.amr_report(g, res, wall_relax, t_inj, ups0)
+    rep["profile_at_end"] = WL.step_profile(g)
     line = {"workload": "amr264x36x96_L%d" % args.max_level, "precision": args.precision, **rep}
     print(json.dumps(line), flush=True)
     return 0
@@ -260,6 +263,7 @@ def run_ensemble_workload(args):
     res = WL.run_cme(g, draws, t_inj=t_inj, hours_after=args.hours, regrid_every=args.regrid_every,
                      max_levels=[d["max_level"] for d in draws], stop_hours_after_arrival=6.0)
     rep = WL.amr_report(g, res, wall_relax, t_inj, ups0)
+    rep["profile_at_end"] = WL.step_profile(g)
     print(json.dumps({"workload": f"ensemble{args.members}_amr264x36x96", "precision": "fp32",
                       "hours_after_injection": args.hours, "max_levels": [d["max_level"] for d in draws], **rep}),
           flush=True)
@@ -283,16 +287,19 @@ def run_tt1au_workload(args):
     g.inject_cone_cme(0, t_start=t_inj, **I.cme_config2(seed=7))
     # labels one regrid ahead at the interval the learned run uses
     recs = H.collect_regrids(g, n_regrids=args.train_regrids, regrid_every=2 * args.regrid_every, crit=WL.CRIT)
-    X, T = H.training_pairs(recs, max_level=L)
-    pos_frac = float(T.mean())
-    X, T = H.rebalance(X, T, seed=2)
+    X0, T0 = H.training_pairs(recs, max_level=L)
+    pos_frac = float(T0.mean())
+    X, T = H.rebalance(X0, T0, seed=2)
     g.mlp_set_params(I.mlp_init(5).astype(np.float32))
     g.mlp_dataset_clear()
     g.mlp_dataset_add(X, T)
     w0 = time.perf_counter()
     losses = g.mlp_train(len(T), epochs=100, batch=1024, lr=1e-3, seed=1)
     train_s = time.perf_counter() - w0
-    theta = g.mlp_get_params()
+    # decision threshold with the best F1 on the unbalanced training pairs,
+    # folded into the output bias (the library decides at probability 1/2)
+    thr, f1 = H.calibrate_threshold(g.mlp_predict(X0), T0)
+    theta = H.shift_output_bias(g.mlp_get_params(), thr)
     del g
     out = {}
     B = args.batch
@@ -300,7 +307,7 @@ def run_tt1au_workload(args):
                                            (f"fp32_learned_batch{B}", FP32_MIXED, True, 2 * args.regrid_every, B),
                                            ("fp32_plain", FP32_MIXED, False, args.regrid_every, 1),
                                            ("fp64_plain", FP64, False, args.regrid_every, 1)):
-        if nm < 2 and name.startswith("fp32_learned_batch"):
+        if (nm < 2 and name.startswith("fp32_learned_batch")) or name.split("_batch")[0] not in args.arms.split(","):
             continue
         g = WL.amr_grid(n_members=nm, max_level=L, precision=prec, max_blocks=max(args.max_blocks, 15000 * nm))
         if learned:
@@ -323,16 +330,18 @@ def run_tt1au_workload(args):
         out[name] = rep
         print(json.dumps({"arm": name, **{k: v for k, v in rep.items() if k != "series_at_earth"}}), flush=True)
         del g
-    a32, a64 = out["fp32_learned"]["arrival_h"][0], out["fp64_plain"]["arrival_h"][0]
+    arr = lambda k: out[k]["arrival_h"][0] if k in out else None
+    a32, a64 = arr("fp32_learned"), arr("fp64_plain")
     # FP32 against FP64 along the Earth probe series (both plain flags)
-    s32, s64 = out["fp32_plain"]["series_at_earth"], out["fp64_plain"]["series_at_earth"]
     serr = {}
-    for key in ("vr_kms", "n"):
-        x, y = np.asarray(s32[key]), np.asarray(s64[key])
-        serr[key + "_max_abs_diff"] = float(np.max(np.abs(x - y)))
-        serr[key + "_max_rel_diff"] = float(np.max(np.abs(x - y)) / np.max(np.abs(y)))
+    if "fp32_plain" in out and "fp64_plain" in out:
+        s32, s64 = out["fp32_plain"]["series_at_earth"], out["fp64_plain"]["series_at_earth"]
+        for key in ("vr_kms", "n"):
+            x, y = np.asarray(s32[key]), np.asarray(s64[key])
+            serr[key + "_max_abs_diff"] = float(np.max(np.abs(x - y)))
+            serr[key + "_max_rel_diff"] = float(np.max(np.abs(x - y)) / np.max(np.abs(y)))
     print(json.dumps({"workload": f"tt1au_amr264x36x96_L{L}", "train_pairs": int(len(T)),
-                      "label_positive_fraction": pos_frac,
+                      "label_positive_fraction": pos_frac, "threshold": thr, "train_f1": f1,
                       "train_loss": [float(losses[0]), float(losses[-1])], "train_s": train_s, **out,
                       "fp32_vs_fp64_series": serr,
                       "arrival_diff_h": None if (a32 is None or a64 is None) else abs(a32 - a64)}), flush=True)

@@ -169,7 +169,10 @@ icarus_status icarus_set_flags(icarus_ctx *ctx, const int8_t *flags);
 /* Apply the current flags: refine +1 leaves by one level, coarsen complete
  * sibling families all flagged -1 (refinement wins), enforce 2:1 balance over
  * faces, edges and corners (least balanced refinement), prolong new children
- * conservatively, restrict coarsened parents, renumber leaves in Morton order. */
+ * conservatively, restrict coarsened parents, renumber leaves in Morton order.
+ * Errors: ICARUS_ERR_CAPACITY if the new tree of all members needs more
+ * blocks than max_blocks; the tree, the state and the flags are then left as
+ * they were (the caller may retry at a later regrid). */
 icarus_status icarus_regrid(icarus_ctx *ctx);
 
 /* Sample primitives at n_pts points rtp[n_pts][3] (host: r, colat, lon) by

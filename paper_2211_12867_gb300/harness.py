@@ -19,6 +19,9 @@ from dataclasses import dataclass, field
 import numpy as np
 
 from . import inputs as I
+from .icarus import IcarusError
+
+CAPACITY = 7   # ICARUS_ERR_CAPACITY
 
 
 # ---------------------------------------------------------------- analysis
@@ -154,6 +157,29 @@ def rebalance(X, T, cap=65536, seed=0):
     return X[sel], T[sel]
 
 
+def calibrate_threshold(prob, T):
+    """Probability threshold with the best F1 score on (unbalanced) labelled
+    pairs: a network trained on a rebalanced set over-predicts the rare
+    class at 1/2."""
+    prob, T = np.asarray(prob, np.float64), np.asarray(T) > 0.5
+    best_t, best_f = 0.5, -1.0
+    for t in np.unique(np.quantile(prob, np.linspace(0.5, 0.9999, 400))):
+        pred = prob > t
+        tp = np.sum(pred & T)
+        f = 2.0 * tp / max(1, pred.sum() + T.sum())
+        if f > best_f:
+            best_t, best_f = float(t), f
+    return best_t, best_f
+
+
+def shift_output_bias(theta, threshold):
+    """Parameters whose sigmoid output crosses 1/2 where the original one
+    crosses `threshold` (the output bias is the last parameter)."""
+    th = np.array(theta, dtype=np.float32, copy=True)
+    th[-1] -= np.float32(math.log(threshold / (1.0 - threshold)))
+    return th
+
+
 # ---------------------------------------------------------------- driver
 @dataclass
 class RunResult:
@@ -168,6 +194,7 @@ class RunResult:
     leaves: list = field(default_factory=list)   # leaves per regrid (all members)
     wall_s: float = 0.0
     wall_at: np.ndarray = None  # wall clock [s] since injection at each sample
+    capacity_skips: int = 0     # regrids refused for want of blocks
 
     def wall_to(self, t):
         """Wall clock from injection until simulated time t (interpolated
@@ -199,7 +226,14 @@ def advance_to(g, t_target, max_steps=1_000_000, regrid_every=0, crit=None, coun
             if on_regrid is not None:
                 flags = on_regrid(g, flags)
                 g.set_flags(flags)
-            g.regrid()
+            try:
+                g.regrid()
+            except IcarusError as e:
+                # the block pool cannot hold the refined tree: the tree (and
+                # the state) stay as they are until a later regrid fits
+                if e.code != CAPACITY:
+                    raise
+                counters["capacity_skips"] = counters.get("capacity_skips", 0) + 1
             counters["since"] = 0
             counters["regrids"] += 1
             counters["leaves"].append(g.n_leaves(-1))
@@ -245,4 +279,4 @@ def propagate(g, cmes, *, t_inj, duration, sample=None, earth_lon0=math.pi, regr
     wid = [shock_width(times, series[m, :, 1], a) for m, a in zip(range(nm), arr)]
     pk = [peak_speed(times, series[m, :, 1], a) for m, a in zip(range(nm), arr)]
     return RunResult(times, series, bg, arr, wid, pk, counters["steps"], counters["regrids"],
-                     counters["leaves"], wall, wall_at)
+                     counters["leaves"], wall, wall_at, counters.get("capacity_skips", 0))

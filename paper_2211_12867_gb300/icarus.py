@@ -344,10 +344,17 @@ class Icarus:
         return out
 
     def mlp_predict(self, X):
+        """Probabilities of host feature rows (sent in batches of 4096, the
+        entry point's limit)."""
         X = np.ascontiguousarray(X, dtype=np.float32).reshape(-1, 64)
         y = np.zeros(X.shape[0], dtype=np.float32)
-        _chk("icarus_mlp_predict", self._mlp("icarus_mlp_predict", C.c_void_p, C.c_int, C.c_void_p)(
-            self.ctx, X.ctypes.data_as(C.c_void_p), X.shape[0], y.ctypes.data_as(C.c_void_p)))
+        f = self._mlp("icarus_mlp_predict", C.c_void_p, C.c_int, C.c_void_p)
+        for a in range(0, X.shape[0], 4096):
+            xa = np.ascontiguousarray(X[a:a + 4096])
+            ya = np.zeros(xa.shape[0], dtype=np.float32)
+            _chk("icarus_mlp_predict", f(self.ctx, xa.ctypes.data_as(C.c_void_p), xa.shape[0],
+                                         ya.ctypes.data_as(C.c_void_p)))
+            y[a:a + xa.shape[0]] = ya
         return y
 
     def mlp_grad(self, X, T):

@@ -70,6 +70,7 @@ def amr_report(g, res, wall_relax, t_inj, ups0=0.0):
         "shock_width_h": [None if w is None else w / I.hours(1.0) for w in res.width],
         "peak_speed_kms": [None if p is None else p * 100.0 for p in res.peak],
         "relax_wall_s": wall_relax, "status": g.status()[0], "floor_hits": int(g.status()[1]),
+        "capacity_skips": res.capacity_skips,
     }
 
 
@@ -89,3 +90,29 @@ def run_cme(g, cmes, *, t_inj, hours_after=72.0, regrid_every=10, max_levels=Non
     stop = None if stop_hours_after_arrival is None else I.hours(stop_hours_after_arrival)
     return H.propagate(g, cmes, t_inj=t_inj, duration=I.hours(hours_after), sample=I.hours(sample_min / 60.0),
                        regrid_every=regrid_every, crit=crit, stop_after_arrival=stop)
+
+
+def step_profile(g, n_steps=20, crit=None, repeats=3):
+    """Where the time of an AMR step goes: per kernel kind of the step (CUDA
+    events, graph replay off while profiling) and the host-timed cost of one
+    flag + regrid; returns a JSON-ready dict (per step / per regrid)."""
+    from .icarus import PROFILE_KINDS
+    g.profile(True)
+    g.profile_read()
+    g.step(n_steps)
+    ms, cnt = g.profile_read()
+    g.profile(False)
+    tot = float(ms.sum())
+    kinds = {k: {"ms_per_step": float(ms[i]) / n_steps, "launches_per_step": int(cnt[i]) / n_steps,
+                 "share": float(ms[i]) / tot if tot > 0 else None} for i, k in enumerate(PROFILE_KINDS)}
+    t_flag = t_regrid = 0.0
+    for _ in range(repeats):
+        w0 = time.perf_counter()
+        g.flag_refine(**(crit or CRIT))
+        w1 = time.perf_counter()
+        g.regrid()
+        w2 = time.perf_counter()
+        t_flag += w1 - w0
+        t_regrid += w2 - w1
+    return {"kernels_ms_per_step": tot / n_steps, "kernels": kinds, "leaves": g.n_leaves(-1),
+            "flag_ms": 1e3 * t_flag / repeats, "regrid_ms": 1e3 * t_regrid / repeats}

@@ -12,7 +12,9 @@ from gpu_common import make_pair, rel_linf, wind_setup
 from paper_2211_12867_gb300.icarus import set_fp64_islands
 
 pytestmark = pytest.mark.gpu
-OUT = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "gpurun_out")
+# reports of measured figures go to $ICARUS_REPORT_DIR (default: reports/)
+OUT = os.environ.get("ICARUS_REPORT_DIR",
+                     os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "reports"))
 
 
 @pytest.mark.parametrize("islands", [(0.05, 0.1), (0.002, 0.1), (0.0, 0.0)])

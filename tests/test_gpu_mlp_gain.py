@@ -26,7 +26,9 @@ from paper_2211_12867_gb300 import workloads as WL
 from paper_2211_12867_gb300.icarus import FP32_MIXED
 
 pytestmark = pytest.mark.gpu
-OUT = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "gpurun_out")
+# reports of measured figures go to $ICARUS_REPORT_DIR (default: reports/)
+OUT = os.environ.get("ICARUS_REPORT_DIR",
+                     os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "reports"))
 
 
 def test_learned_preflags_reduce_missed_refinements():

@@ -106,3 +106,17 @@ def test_rebalance_repeats_rare_positives():
     # every sample is an original pair, positives stay positive
     assert np.all(T[Xb[:, 0].astype(int)] == Tb)
     assert set(Xb[Tb > 0, 0].astype(int)) == {3, 500, 900}
+
+
+def test_threshold_calibration_and_bias_shift():
+    rng = np.random.default_rng(0)
+    T = (rng.uniform(size=5000) < 0.02).astype(np.float32)
+    # scores: positives mostly above 0.8, negatives spread below 0.9
+    prob = np.where(T > 0, rng.uniform(0.75, 1.0, 5000), rng.uniform(0.0, 0.9, 5000))
+    t, f = H.calibrate_threshold(prob, T)
+    assert 0.8 < t < 0.95 and f > 0.5
+    theta = np.zeros(10, np.float32)
+    th = H.shift_output_bias(theta, 0.8)
+    # sigmoid(z + b') = 1/2 exactly where sigmoid(z + b) = 0.8
+    z = math.log(0.8 / 0.2)
+    assert abs(z + th[-1]) < 1e-6
