@@ -703,7 +703,7 @@ StageLaunch stage_cfg(icarus_ctx *c, int stage2) {
     segs = std::max(1LL, std::min<long long>(segs, c->d.block[0] / 8 > 0 ? c->d.block[0] / 8 : 1));
     seg = (c->d.block[0] + (int)segs - 1) / (int)segs;
   }
-  seg = std::max(1, std::min(seg, c->d.block[0]));
+  seg = std::max(1, std::min(std::min(seg, c->d.block[0]), STAGE_SEG_MAX));
   sl.seg_len = seg;
   sl.segs = (c->d.block[0] + seg - 1) / seg;
   sl.list = c->all_list;

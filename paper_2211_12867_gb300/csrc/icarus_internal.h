@@ -114,6 +114,9 @@ struct StageLaunch {
   int grid;           // CTAs (persistent loop)
 };
 int stage_launch(const KParams &kp, const StageLaunch &sl, int precision, cudaStream_t s);
+// longest radial segment a stage work item marches (its geometry is staged
+// in shared memory)
+constexpr int STAGE_SEG_MAX = 64;
 size_t stage_smem_bytes(int precision, int tj, int tk);
 int stage_tile_supported(int precision, int tj, int tk);
 int stage_max_ctas_per_sm(int precision, int tj, int tk);

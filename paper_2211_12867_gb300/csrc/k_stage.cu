@@ -35,7 +35,12 @@ struct StageSmem {
   static constexpr size_t bytes(int tj, int tk) {
     return sizeof(real) * (size_t)(5 * NVAR * (tj + 4) * (tk + 4) + 2 * NVAR * (tj + 1) * tk +
                                    2 * NVAR * tj * (tk + 1) + 4 * (tj + 2) * (tk + 2) +
-                                   NVAR * ((tj * tk + 31) / 32 * 32));
+                                   NVAR * ((tj * tk + 31) / 32 * 32) + geo(tj, tk));
+  }
+  // geometry of one work item: 4 plane arrays and the faces in r, 5 row
+  // arrays and the faces in theta, the phi centres
+  static constexpr int geo(int tj, int tk) {
+    return 4 * (STAGE_SEG_MAX + 4) + (STAGE_SEG_MAX + 5) + 5 * (tj + 4) + (tj + 5) + (tk + 4);
   }
 };
 
@@ -101,9 +106,19 @@ __device__ __forceinline__ real el(const real *a, int v, int q) {
 // threads per CTA: the tile's cells rounded up to whole warps (the extra
 // threads own no cell but share the loads and the face fluxes)
 constexpr int stage_threads(int tj, int tk) { return (tj * tk + 31) / 32 * 32; }
+constexpr int cmin(int a, int b) { return a < b ? a : b; }
+constexpr int cmax(int a, int b) { return a > b ? a : b; }
+// resident CTAs per SM the register budget is sized for (FP32): as many as
+// the shared memory of an SM (228 KB, 1 KB reserved per CTA) holds, and no
+// more than leave 128 registers a thread; at least 2.  FP64: 1.
+constexpr int stage_min_ctas(int real_bytes, int tj, int tk) {
+  return real_bytes != 4 ? 1
+                         : cmax(2, cmin(65536 / (stage_threads(tj, tk) * 128),
+                                        (int)(233472 / (StageSmem<float>::bytes(tj, tk) + 1024))));
+}
 
 template <typename real, int TJ, int TK, bool S2>
-__global__ void __launch_bounds__(stage_threads(TJ, TK), (sizeof(real) == 4 ? 2 : 1))
+__global__ void __launch_bounds__(stage_threads(TJ, TK), stage_min_ctas(sizeof(real), TJ, TK))
     k_stage(const KParams kp, const StageLaunch sl) {
   constexpr int NT = stage_threads(TJ, TK), RJ = TJ + 4, RK = TK + 4, RP = RJ * RK;
   constexpr int DJ = TJ + 2, DK = TK + 2, DP = DJ * DK;
@@ -114,6 +129,14 @@ __global__ void __launch_bounds__(stage_threads(TJ, TK), (sizeof(real) == 4 ? 2 
   real *fph = fth + 2 * NVAR * NTH;     // two buffers of phi-face fluxes
   real *dring = fph + 2 * NVAR * NPH;
   real *u0s = dring + 4 * DP;           // U^n of the thread's own cell, next plane
+  // geometry of the work item (plane arrays from plane ib-2, row arrays from
+  // row -2 of the tile, phi centres from column -2)
+  constexpr int NRP = STAGE_SEG_MAX + 4, NJ = TJ + 4;
+  real *s_rc = u0s + NVAR * NT, *s_dr = s_rc + NRP, *s_dr2 = s_dr + NRP, *s_dr3 = s_dr2 + NRP;
+  real *s_r2f = s_dr3 + NRP;                                  // STAGE_SEG_MAX + 5 faces
+  real *s_tc = s_r2f + NRP + 1, *s_st = s_tc + NJ, *s_ct = s_st + NJ, *s_dcos = s_ct + NJ, *s_dth = s_dcos + NJ;
+  real *s_sinf = s_dth + NJ;                                  // TJ + 5 faces
+  real *s_pc = s_sinf + NJ + 1;                               // TK + 4
 
   const int tid = threadIdx.x, jl = tid / TK, kl = tid % TK;
   const real gamma = (real)kp.gamma, pfl = (real)kp.p_floor, rfl = (real)kp.rho_floor;
@@ -160,7 +183,6 @@ __global__ void __launch_bounds__(stage_threads(TJ, TK), (sizeof(real) == 4 ? 2 
     real *Uout = reinterpret_cast<real *>(sl.Uout) + (size_t)slot * bstride;
     const bool valid = tid < TJ * TK && jl < nvj && kl < nvk;
     const int j = j0 + jl, k = k0 + kl;           // interior indices in the block
-    const int J = J0 + jl, K = K0 + kl;           // global indices at the level
 
     // Planes of U_in are copied asynchronously (cp.async, 2 cells x 8
     // variables per unit) straight into their ring slot and converted to
@@ -243,8 +265,8 @@ __global__ void __launch_bounds__(stage_threads(TJ, TK), (sizeof(real) == 4 ? 2 
     auto divb_plane = [&](int p) {
       real *dst = dring + (p & 3) * DP;
       const real *pm = ringp(p - 1), *pc = ringp(p), *pp = ringp(p + 1);
-      const int I = I0 + p;
-      const real rcm = G.rc[I - 1 + NGH], rcc = G.rc[I + NGH], rcp = G.rc[I + 1 + NGH];
+      const int pr = p - ib + 2;   // plane index in the staged arrays
+      const real rcm = s_rc[pr - 1], rcc = s_rc[pr], rcp = s_rc[pr + 1];
       // plane-uniform radial factors
       const real wm = spherical ? rcm * rcm : real(1), wp = spherical ? rcp * rcp : real(1);
       const real fr = RT<real>::rcp_((spherical ? rcc * rcc : real(1)) * (rcp - rcm));
@@ -252,17 +274,16 @@ __global__ void __launch_bounds__(stage_threads(TJ, TK), (sizeof(real) == 4 ? 2 
         const int dj = q / DK - 1, dk = q - (q / DK) * DK - 1;
         if (dj > nvj || dk > nvk) continue;
         const int jj = dj + 2, kk = dk + 2;
-        const int Jg = J0 + dj, Kg = K0 + dk;
         const int o = jj * RK + kk;
         const real brm = el<real, RP>(pm, 5, o), brp = el<real, RP>(pp, 5, o);
         const real btm = el<real, RP>(pc, 6, o - RK), btp = el<real, RP>(pc, 6, o + RK);
         const real bpm = el<real, RP>(pc, 7, o - 1), bpp = el<real, RP>(pc, 7, o + 1);
-        const real tcm = G.tc[Jg - 1 + NGH], tcp = G.tc[Jg + 1 + NGH];
-        const real pcm = G.pc[Kg - 1 + NGH], pcp = G.pc[Kg + 1 + NGH];
+        const real tcm = s_tc[dj + 1], tcp = s_tc[dj + 3];
+        const real pcm = s_pc[dk + 1], pcp = s_pc[dk + 3];
         real div;
         if (spherical) {
-          const real stc = G.sintc[Jg + NGH];
-          const real sm = G.sintc[Jg - 1 + NGH], sp = G.sintc[Jg + 1 + NGH];
+          const real stc = s_st[dj + 2];
+          const real sm = s_st[dj + 1], sp = s_st[dj + 3];
           const real irs = RT<real>::rcp_(rcc * stc);
           div = (wp * brp - wm * brm) * fr + (sp * btp - sm * btm) * irs * RT<real>::rcp_(tcp - tcm) +
                 (bpp - bpm) * irs * RT<real>::rcp_(pcp - pcm);
@@ -272,6 +293,31 @@ __global__ void __launch_bounds__(stage_threads(TJ, TK), (sizeof(real) == 4 ? 2 
         dst[q] = div;
       }
     };
+
+    // ---- geometry of the work item into shared memory (read after the
+    // prologue's first barrier); rows / columns past the block's edge are
+    // never read and not loaded ----
+    {
+      const int npl = ie - ib + 4, ir0 = I0 + ib - 2 + NGH;
+      for (int q = tid; q < npl; q += NT) {
+        s_rc[q] = G.rc[ir0 + q];
+        s_dr[q] = G.dr[ir0 + q];
+        s_dr2[q] = G.dr2[ir0 + q];
+        s_dr3[q] = G.dr3[ir0 + q];
+      }
+      for (int q = tid; q <= npl; q += NT) s_r2f[q] = G.r2f[ir0 + q];
+      const int jr0 = J0 - 2 + NGH;
+      for (int q = tid; q < nvj + 4; q += NT) {
+        s_tc[q] = G.tc[jr0 + q];
+        s_st[q] = G.sintc[jr0 + q];
+        s_ct[q] = G.costc[jr0 + q];
+        s_dcos[q] = G.dcos[jr0 + q];
+        s_dth[q] = G.dth[jr0 + q];
+      }
+      for (int q = tid; q <= nvj + 4; q += NT) s_sinf[q] = G.sinf[jr0 + q];
+      for (int q = tid; q < nvk + 4; q += NT) s_pc[q] = G.pc[K0 - 2 + NGH + q];
+    }
+    const real dphi = G.dphi;
 
     // ---- prologue: planes ib-2 .. ib+2 converted, r flux at face ib ----
     for (int p = ib - 2; p <= ib + 2; p++) issue_plane(p);
@@ -346,14 +392,12 @@ __global__ void __launch_bounds__(stage_threads(TJ, TK), (sizeof(real) == 4 ? 2 
         for (int v = 0; v < NVAR; v++) sc[v] = sn[v];
       }
       if (valid) {
-        const int I = I0 + i;
-        const int iI = I + NGH, iJ = J + NGH;
-        const real dphi = G.dphi;
-        const real dcos = G.dcos[iJ], dr2 = G.dr2[iI];
-        const real Arm = G.r2f[iI] * dcos * dphi, Arp = G.r2f[iI + 1] * dcos * dphi;
-        const real Atm = G.sinf[iJ] * dr2 * dphi, Atp = G.sinf[iJ + 1] * dr2 * dphi;
-        const real Ap = dr2 * G.dth[iJ];
-        const real V = G.dr3[iI] * dcos * dphi;
+        const int pr = i - ib + 2, jr = jl + 2;   // indices in the staged arrays
+        const real dcos = s_dcos[jr], dr2 = s_dr2[pr];
+        const real Arm = s_r2f[pr] * dcos * dphi, Arp = s_r2f[pr + 1] * dcos * dphi;
+        const real Atm = s_sinf[jr] * dr2 * dphi, Atp = s_sinf[jr + 1] * dr2 * dphi;
+        const real Ap = dr2 * s_dth[jr];
+        const real V = s_dr3[pr] * dcos * dphi;
         const real iV = RT<real>::rcp_(V);
         real w[NVAR];
         gather(ringp(i), jl + 2, kl + 2, w);
@@ -387,27 +431,26 @@ __global__ void __launch_bounds__(stage_threads(TJ, TK), (sizeof(real) == 4 ? 2 
           un[3] += (-rho * vr * vp + Br * Bp) * ir - (rho * vt * vp - Bt * Bp) * gt;
           un[6] += (vr * Bt - vt * Br) * ir;
           un[7] += (vr * Bp - vp * Br) * ir + (vt * Bp - vp * Bt) * gt;
-          const real rc = G.rc[iI], st = G.sintc[iJ], ct = G.costc[iJ];
+          const real rc = s_rc[pr], st = s_st[jr], ct = s_ct[jr];
           const real vs = vr * st + vt * ct;
           un[1] += rho * (real(2) * Om * vp * st + Om * Om * rc * st * st);
           un[2] += rho * (real(2) * Om * vp * ct + Om * Om * rc * st * ct);
           un[3] += real(-2) * Om * rho * vs;
           un[4] += rho * Om * Om * rc * st * vs;
         }
-#pragma unroll
         cp_async_wait_group<0>();   // this thread's U^n copy of plane i
 #pragma unroll
         for (int v = 0; v < NVAR; v++) un[v] = u0s[v * NT + tid] + dt * un[v];
         if (S2 && Cd > real(0)) {
           const real *dm = dring + ((i - 1) & 3) * DP, *dc = dring + (i & 3) * DP, *dp = dring + ((i + 1) & 3) * DP;
           const int q = (jl + 1) * DK + (kl + 1);
-          const real rcm = G.rc[iI - 1], rcc = G.rc[iI], rcp = G.rc[iI + 1];
-          const real tcm = G.tc[iJ - 1], tcp = G.tc[iJ + 1];
-          const real pcm = G.pc[K - 1 + NGH], pcp = G.pc[K + 1 + NGH];
-          const real dr = G.dr[iI], dth = G.dth[iJ];
+          const real rcm = s_rc[pr - 1], rcc = s_rc[pr], rcp = s_rc[pr + 1];
+          const real tcm = s_tc[jr - 1], tcp = s_tc[jr + 1];
+          const real pcm = s_pc[kl + 1], pcp = s_pc[kl + 3];
+          const real dr = s_dr[pr], dth = s_dth[jr];
           real gr_, gt_, gp_, h2inv;
           if (spherical) {
-            const real st = G.sintc[iJ];
+            const real st = s_st[jr];
             const real irc = RT<real>::rcp_(rcc), irs = RT<real>::rcp_(rcc * st);
             gr_ = (dp[q] - dm[q]) * RT<real>::rcp_(rcp - rcm);
             gt_ = (dc[q + DK] - dc[q - DK]) * irc * RT<real>::rcp_(tcp - tcm);
@@ -441,10 +484,10 @@ __global__ void __launch_bounds__(stage_threads(TJ, TK), (sizeof(real) == 4 ? 2 
           if (!skip) {
             real wn[NVAR];
             cons2prim_speed<real>(un, wn, gamma, pfl);
-            real dx0 = G.dr[iI], dx1 = G.dth[iJ], dx2 = G.dphi;
+            real dx0 = s_dr[pr], dx1 = s_dth[jr], dx2 = dphi;
             if (spherical) {
-              dx1 *= G.rc[iI];
-              dx2 *= G.rc[iI] * G.sintc[iJ];
+              dx1 *= s_rc[pr];
+              dx2 *= s_rc[pr] * s_st[jr];
             }
             const real s = (RT<real>::abs_(wn[1]) + fast_speed<real, 0>(wn, gamma)) * RT<real>::rcp_(dx0) +
                            (RT<real>::abs_(wn[2]) + fast_speed<real, 1>(wn, gamma)) * RT<real>::rcp_(dx1) +
