@@ -65,12 +65,13 @@ def parse():
     p.add_argument("--islands", default="0.002,0.1",
                    help="FP32 mode: FP64 pressure where p < a*e or p < b*B^2/2 ('a,b')")
     p.add_argument("--tile", default="", help="force the stage tile 'tile_theta,tile_phi,r_segment'")
-    p.add_argument("--workload", default="wedge", choices=["wedge", "amr", "ensemble", "tt1au"],
+    p.add_argument("--workload", default="wedge", choices=["wedge", "amr", "ensemble", "tt1au", "learned5"],
                    help="amr / ensemble / tt1au: stretched AMR CME runs (one JSON line of their own)")
     p.add_argument("--members", type=int, default=32)
     p.add_argument("--max-blocks", type=int, default=60000)
     p.add_argument("--train-regrids", type=int, default=60)
     p.add_argument("--batch", type=int, default=8, help="tt1au: members of the batched learned arm")
+    p.add_argument("--window-regrids", type=int, default=60, help="learned5: regrids after injection")
     p.add_argument("--arms", default="fp32_learned,fp32_plain,fp64_plain",
                    help="tt1au arms (fp32_learned, fp32_learned_batch, fp32_plain, fp64_plain)")
     p.add_argument("--max-level", type=int, default=4)
@@ -348,6 +349,51 @@ def run_tt1au_workload(args):
     return 0
 
 
+def run_learned5_workload(args):
+    """AMR level 5 with the learned pre-flagger: trained on the GPU from the
+    regrids of a level-4 run of another CME draw (labels: refinable flags one
+    regrid ahead), then applied at every regrid of a level-5 run of the
+    headline CME over a window after injection; reports the block counts,
+    the missed-flag rates of the learned and the plain pre-flags, and the
+    throughput."""
+    import torch
+    from paper_2211_12867_gb300 import harness as H
+    from paper_2211_12867_gb300 import workloads as WL
+    from paper_2211_12867_gb300.icarus import FP32_MIXED
+    torch.cuda.set_device(0)
+    every = 2 * args.regrid_every
+    g = WL.amr_grid(max_level=4, precision=FP32_MIXED, max_blocks=args.max_blocks)
+    WL.start_wind(g)
+    t_inj, _ = WL.relax(g, args.relax_days)
+    g.inject_cone_cme(0, t_start=t_inj, **I.cme_config2(seed=7))
+    recs = H.collect_regrids(g, n_regrids=args.train_regrids, regrid_every=every, crit=WL.CRIT)
+    X0, T0 = H.training_pairs(recs, max_level=4)
+    X, T = H.rebalance(X0, T0, seed=2)
+    g.mlp_set_params(I.mlp_init(5).astype(np.float32))
+    g.mlp_dataset_clear()
+    g.mlp_dataset_add(X, T)
+    losses = g.mlp_train(len(T), epochs=100, batch=1024, lr=1e-3, seed=1)
+    thr, f1 = H.calibrate_threshold(g.mlp_predict(X0), T0)
+    theta = H.shift_output_bias(g.mlp_get_params(), thr)
+    del g
+    g = WL.amr_grid(max_level=5, precision=FP32_MIXED, max_blocks=args.max_blocks)
+    g.mlp_set_params(theta)
+    WL.start_wind(g)
+    t_inj, wall_relax = WL.relax(g, args.relax_days)
+    g.inject_cone_cme(0, t_start=t_inj, **I.cme_config2(seed=0))
+    ups0 = float(np.sum(g.cell_updates()))
+    rep = WL.run_learned_window(g, n_regrids=args.window_regrids, regrid_every=every, max_level=5)
+    ups = float(np.sum(g.cell_updates())) - ups0
+    t_end = g.step(0)[0]
+    print(json.dumps({"workload": "learned_amr264x36x96_L5", "train_pairs": int(len(T0)),
+                      "label_positive_fraction": float(T0.mean()), "threshold": thr, "train_f1": f1,
+                      "train_loss": [float(losses[0]), float(losses[-1])],
+                      "hours_after_injection": (t_end - t_inj) / I.hours(1.0), "cell_updates": ups,
+                      "cell_updates_per_s": ups / rep["wall_s"], "relax_wall_s": wall_relax,
+                      "status": g.status()[0], **rep}), flush=True)
+    return 0
+
+
 def main():
     args = parse()
     if args.impl == "reference":
@@ -358,6 +404,8 @@ def main():
         return run_ensemble_workload(args)
     if args.workload == "tt1au":
         return run_tt1au_workload(args)
+    if args.workload == "learned5":
+        return run_learned5_workload(args)
     import torch
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))

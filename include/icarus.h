@@ -72,7 +72,7 @@ enum { ICARUS_FLAG_PLAIN = 0, ICARUS_FLAG_LEARNED = 1, ICARUS_FLAG_BOTH = 2 };
 
 /* Grid descriptor.
  *   n_cells      base-level cells (r, theta, phi); must be multiples of block.
- *   block        interior cells per block and direction, even, >= 4.
+ *   block        interior cells per block and direction, even, 4 .. 1020.
  *   max_level    finest level (1 = no refinement); per member, see
  *                icarus_set_member_max_level.  At most 8.
  *   radial_stretch  1: geometric radial faces r_I = r_in (r_out/r_in)^(I/N)
@@ -305,6 +305,26 @@ icarus_status icarus_profile(icarus_ctx *ctx, int enable);
  * stage, 5 reflux, 6 dt finalize.  ms and count hold nkinds entries (<= 7).
  * Synchronises the stream. */
 icarus_status icarus_profile_read(icarus_ctx *ctx, double *ms, int *count, int nkinds);
+
+/* Checkpoint and resume (the paper runs for days of simulated time; it has no
+ * passage on checkpoints).  icarus_save writes to the host file `path`
+ * everything a step reads: the descriptor fields that fix grid and physics,
+ * per member its finest level, cone CME, leaf tree, time, CFL time step and
+ * cell-update count, the inner-boundary maps and background speeds, the
+ * leaves' state in the working precision, the FP64-island thresholds, the
+ * floor-hit count and the pre-flagger's parameters if set (not its Adam
+ * moments).  Binary, host byte order.  Synchronises the stream.
+ * icarus_load reads such a file into a context created with the same
+ * descriptor (n_cells, block, max_level, stretch, geometry, extents, gamma,
+ * omega, cfl, divb_cd, floors, precision, n_members, boundaries; max_blocks
+ * and the arena may differ): stepping then continues bit for bit as the
+ * saved context would have.  Errors: ICARUS_ERR_ARG if the file cannot be
+ * opened, is not a checkpoint of this version or does not match the
+ * descriptor (the context is then unchanged); ICARUS_ERR_CAPACITY if its
+ * leaves exceed max_blocks (unchanged).  A successful load clears a
+ * poisoned context's status word. */
+icarus_status icarus_save(icarus_ctx *ctx, const char *path);
+icarus_status icarus_load(icarus_ctx *ctx, const char *path);
 
 void icarus_destroy(icarus_ctx *ctx);
 const char *icarus_status_string(icarus_status s);

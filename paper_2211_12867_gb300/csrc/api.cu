@@ -91,7 +91,7 @@ icarus_status validate(const icarus_grid_desc *d) {
   if (d->precision != ICARUS_FP64 && d->precision != ICARUS_FP32_MIXED) return ICARUS_ERR_ARG;
   if (d->geometry != ICARUS_SPHERICAL && d->geometry != ICARUS_CARTESIAN) return ICARUS_ERR_ARG;
   for (int k = 0; k < 3; k++) {
-    if (d->block[k] < 4 || d->block[k] % 2) return ICARUS_ERR_ARG;
+    if (d->block[k] < 4 || d->block[k] % 2 || d->block[k] + 2 * NGH > 1024) return ICARUS_ERR_ARG;
     if (d->n_cells[k] < d->block[k] || d->n_cells[k] % d->block[k]) return ICARUS_ERR_ARG;
     if (!(d->x_max[k] > d->x_min[k])) return ICARUS_ERR_ARG;
     if ((d->bc_lo[k] == ICARUS_BC_PERIODIC) != (d->bc_hi[k] == ICARUS_BC_PERIODIC)) return ICARUS_ERR_ARG;
@@ -966,7 +966,7 @@ icarus_status icarus_init_grid(const icarus_grid_desc *desc, icarus_ctx **out) {
         for (int k = 0; k < P2; k++) {
           const bool in = i >= NGH && i < NGH + desc->block[0] && j >= NGH && j < NGH + desc->block[1] && k >= NGH &&
                           k < NGH + desc->block[2];
-          if (!in) sh.push_back((i * P1 + j) * P2 + k);
+          if (!in) sh.push_back((i << 20) | (j << 10) | k);   // packed padded index
         }
     if (cudaMemcpyAsync(c->shell, sh.data(), sizeof(int) * sh.size(), cudaMemcpyHostToDevice, c->stream) !=
             cudaSuccess ||
@@ -1613,3 +1613,204 @@ icarus_status icarus_mlp_train(icarus_ctx *c, int n_train, int epochs, int batch
 
 }  // extern "C"
 
+
+// ======================================================================
+// Checkpoint / resume.  A checkpoint holds everything a step reads: the
+// descriptor fields that fix the grid and the physics (checked on load), per
+// member its finest level, cone CME, leaf tree, time, CFL time step and
+// cell-update count, the inner-boundary maps and background speeds, the
+// leaves' state in the working precision (with ghosts), the FP64-island
+// thresholds, the floor-hit count and, if set, the pre-flagger's parameters.
+namespace {
+
+const char CK_MAGIC[8] = {'I', 'C', 'A', 'R', 'U', 'S', 'C', 'K'};
+const uint32_t CK_VERSION = 1;
+
+// the descriptor fields a checkpoint must agree on, in a fixed order
+std::vector<double> ck_fingerprint(const icarus_grid_desc &d) {
+  std::vector<double> f;
+  for (int k = 0; k < 3; k++) f.push_back(d.n_cells[k]);
+  for (int k = 0; k < 3; k++) f.push_back(d.block[k]);
+  f.push_back(d.max_level);
+  f.push_back(d.radial_stretch);
+  f.push_back(d.geometry);
+  for (int k = 0; k < 3; k++) f.push_back(d.x_min[k]);
+  for (int k = 0; k < 3; k++) f.push_back(d.x_max[k]);
+  f.push_back(d.gamma);
+  f.push_back(d.omega);
+  f.push_back(d.cfl);
+  f.push_back(d.divb_cd);
+  f.push_back(d.p_floor);
+  f.push_back(d.rho_floor);
+  f.push_back(d.precision);
+  f.push_back(d.n_members);
+  for (int k = 0; k < 3; k++) f.push_back(d.bc_lo[k]);
+  for (int k = 0; k < 3; k++) f.push_back(d.bc_hi[k]);
+  return f;
+}
+
+struct CkFile {
+  FILE *f = nullptr;
+  bool ok = true;
+  ~CkFile() {
+    if (f) fclose(f);
+  }
+  void put(const void *p, size_t n) {
+    if (ok && n && fwrite(p, 1, n, f) != n) ok = false;
+  }
+  void get(void *p, size_t n) {
+    if (ok && n && fread(p, 1, n, f) != n) ok = false;
+  }
+};
+
+size_t slot_bytes(const icarus_ctx *c) { return (size_t)NVAR * c->kp.pcells * c->rsize; }
+
+}  // namespace
+
+extern "C" {
+
+icarus_status icarus_save(icarus_ctx *c, const char *path) {
+  if (!c || !path) return ICARUS_ERR_ARG;
+  const int nm = c->d.n_members;
+  const size_t nbc = (size_t)c->d.n_cells[0] * c->d.n_cells[1] * c->d.n_cells[2];
+  const size_t nbm = (size_t)NVAR * c->d.n_cells[1] * c->d.n_cells[2];
+  std::vector<double> t(nm), dtc(nm), upd(nm), bmap(nm * nbm), vbg(nm * nbc);
+  unsigned long long hits = 0;
+  std::vector<unsigned char> U(slot_bytes(c) * c->nleaves);
+  std::vector<float> theta(c->mlp_ready ? mlp_n_params() : 0);
+  cudaStream_t s = c->stream;
+  CK(cudaMemcpyAsync(t.data(), c->t, sizeof(double) * nm, cudaMemcpyDeviceToHost, s));
+  CK(cudaMemcpyAsync(dtc.data(), c->dt_cfl, sizeof(double) * nm, cudaMemcpyDeviceToHost, s));
+  CK(cudaMemcpyAsync(upd.data(), c->updates, sizeof(double) * nm, cudaMemcpyDeviceToHost, s));
+  CK(cudaMemcpyAsync(bmap.data(), c->bmap, sizeof(double) * bmap.size(), cudaMemcpyDeviceToHost, s));
+  CK(cudaMemcpyAsync(vbg.data(), c->vbg, sizeof(double) * vbg.size(), cudaMemcpyDeviceToHost, s));
+  CK(cudaMemcpyAsync(&hits, c->floor_hits, sizeof(hits), cudaMemcpyDeviceToHost, s));
+  if (!U.empty()) CK(cudaMemcpyAsync(U.data(), c->U, U.size(), cudaMemcpyDeviceToHost, s));
+  if (!theta.empty())
+    CK(cudaMemcpyAsync(theta.data(), c->mlp_theta, sizeof(float) * theta.size(), cudaMemcpyDeviceToHost, s));
+  CK(cudaStreamSynchronize(s));
+  CkFile F;
+  F.f = fopen(path, "wb");
+  if (!F.f) return ICARUS_ERR_ARG;
+  F.put(CK_MAGIC, 8);
+  F.put(&CK_VERSION, sizeof(CK_VERSION));
+  const std::vector<double> fp = ck_fingerprint(c->d);
+  const uint32_t nfp = (uint32_t)fp.size();
+  F.put(&nfp, sizeof(nfp));
+  F.put(fp.data(), sizeof(double) * fp.size());
+  for (int m = 0; m < nm; m++) {
+    const Member &M = c->mem[m];
+    const int32_t hdr[2] = {M.max_level, (int32_t)M.leaves.size()};
+    F.put(hdr, sizeof(hdr));
+    F.put(&M.cme, sizeof(DevCme));
+    for (const Leaf &l : M.leaves) {
+      const int32_t row[4] = {l.level, l.ix[0], l.ix[1], l.ix[2]};
+      F.put(row, sizeof(row));
+    }
+  }
+  F.put(t.data(), sizeof(double) * nm);
+  F.put(dtc.data(), sizeof(double) * nm);
+  F.put(upd.data(), sizeof(double) * nm);
+  F.put(bmap.data(), sizeof(double) * bmap.size());
+  F.put(vbg.data(), sizeof(double) * vbg.size());
+  F.put(&hits, sizeof(hits));
+  const double isl[2] = {c->isl_pe, c->isl_beta};
+  F.put(isl, sizeof(isl));
+  F.put(U.data(), U.size());
+  const int32_t nth = (int32_t)theta.size();
+  F.put(&nth, sizeof(nth));
+  F.put(theta.data(), sizeof(float) * theta.size());
+  return F.ok ? ICARUS_OK : ICARUS_ERR_ARG;
+}
+
+icarus_status icarus_load(icarus_ctx *c, const char *path) {
+  if (!c || !path) return ICARUS_ERR_ARG;
+  const int nm = c->d.n_members;
+  const size_t nbc = (size_t)c->d.n_cells[0] * c->d.n_cells[1] * c->d.n_cells[2];
+  const size_t nbm = (size_t)NVAR * c->d.n_cells[1] * c->d.n_cells[2];
+  CkFile F;
+  F.f = fopen(path, "rb");
+  if (!F.f) return ICARUS_ERR_ARG;
+  char magic[8];
+  uint32_t ver = 0, nfp = 0;
+  F.get(magic, 8);
+  F.get(&ver, sizeof(ver));
+  F.get(&nfp, sizeof(nfp));
+  const std::vector<double> fp = ck_fingerprint(c->d);
+  if (!F.ok || memcmp(magic, CK_MAGIC, 8) != 0 || ver != CK_VERSION || nfp != fp.size()) return ICARUS_ERR_ARG;
+  std::vector<double> fq(nfp);
+  F.get(fq.data(), sizeof(double) * nfp);
+  if (!F.ok || memcmp(fq.data(), fp.data(), sizeof(double) * nfp) != 0) return ICARUS_ERR_ARG;
+  std::vector<Member> next(nm);
+  size_t total = 0;
+  for (int m = 0; m < nm; m++) {
+    int32_t hdr[2] = {0, 0};
+    F.get(hdr, sizeof(hdr));
+    if (!F.ok || hdr[0] < 1 || hdr[0] > c->d.max_level || hdr[1] < 1) return ICARUS_ERR_ARG;
+    next[m].max_level = hdr[0];
+    F.get(&next[m].cme, sizeof(DevCme));
+    next[m].leaves.resize(hdr[1]);
+    for (Leaf &l : next[m].leaves) {
+      int32_t row[4];
+      F.get(row, sizeof(row));
+      if (!F.ok || row[0] < 1 || row[0] > c->d.max_level) return ICARUS_ERR_ARG;
+      l.level = row[0];
+      for (int d = 0; d < 3; d++) {
+        l.ix[d] = row[1 + d];
+        if (l.ix[d] < 0 || l.ix[d] >= nblk_dim(c, l.level, d)) return ICARUS_ERR_ARG;
+      }
+    }
+    total += next[m].leaves.size();
+  }
+  if (total > (size_t)c->lay.max_blocks) return ICARUS_ERR_CAPACITY;
+  std::vector<double> t(nm), dtc(nm), upd(nm), bmap(nm * nbm), vbg(nm * nbc);
+  unsigned long long hits = 0;
+  double isl[2];
+  F.get(t.data(), sizeof(double) * nm);
+  F.get(dtc.data(), sizeof(double) * nm);
+  F.get(upd.data(), sizeof(double) * nm);
+  F.get(bmap.data(), sizeof(double) * bmap.size());
+  F.get(vbg.data(), sizeof(double) * vbg.size());
+  F.get(&hits, sizeof(hits));
+  F.get(isl, sizeof(isl));
+  std::vector<unsigned char> U(slot_bytes(c) * total);
+  F.get(U.data(), U.size());
+  int32_t nth = 0;
+  F.get(&nth, sizeof(nth));
+  if (!F.ok || (nth != 0 && nth != mlp_n_params())) return ICARUS_ERR_ARG;
+  std::vector<float> theta(nth);
+  F.get(theta.data(), sizeof(float) * nth);
+  if (!F.ok) return ICARUS_ERR_ARG;
+  // everything read: replace the context's state
+  c->mem = std::move(next);
+  for (Member &M : c->mem) build_member_map(c, M);
+  icarus_status st = upload_tree(c, c->blk);
+  if (st != ICARUS_OK) return st;
+  c->isl_pe = isl[0];
+  c->isl_beta = isl[1];
+  fill_kp(c);
+  cudaStream_t s = c->stream;
+  for (int m = 0; m < nm; m++) CK(cudaMemcpyAsync(c->cme + m, &c->mem[m].cme, sizeof(DevCme), cudaMemcpyHostToDevice, s));
+  CK(cudaMemcpyAsync(c->t, t.data(), sizeof(double) * nm, cudaMemcpyHostToDevice, s));
+  CK(cudaMemcpyAsync(c->dt_cfl, dtc.data(), sizeof(double) * nm, cudaMemcpyHostToDevice, s));
+  CK(cudaMemcpyAsync(c->updates, upd.data(), sizeof(double) * nm, cudaMemcpyHostToDevice, s));
+  CK(cudaMemcpyAsync(c->bmap, bmap.data(), sizeof(double) * bmap.size(), cudaMemcpyHostToDevice, s));
+  CK(cudaMemcpyAsync(c->vbg, vbg.data(), sizeof(double) * vbg.size(), cudaMemcpyHostToDevice, s));
+  CK(cudaMemcpyAsync(c->floor_hits, &hits, sizeof(hits), cudaMemcpyHostToDevice, s));
+  CK(cudaMemsetAsync(c->status, 0, sizeof(unsigned int), s));
+  if (!U.empty()) CK(cudaMemcpyAsync(c->U, U.data(), U.size(), cudaMemcpyHostToDevice, s));
+  if (nth) {
+    CK(cudaMemcpyAsync(c->mlp_theta, theta.data(), sizeof(float) * nth, cudaMemcpyHostToDevice, s));
+    CK(cudaMemsetAsync(c->mlp_m, 0, sizeof(float) * nth, s));
+    CK(cudaMemsetAsync(c->mlp_v, 0, sizeof(float) * nth, s));
+    c->mlp_step = 0;
+    c->mlp_ready = true;
+  }
+  CK(cudaStreamSynchronize(s));
+  c->poisoned = false;
+  c->flags_valid = false;
+  c->graph_valid = false;
+  return ICARUS_OK;
+}
+
+}  // extern "C"

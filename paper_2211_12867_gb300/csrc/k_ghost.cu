@@ -88,24 +88,40 @@ __device__ void prolong_value(const KParams &kp, const real *U, int cs, int Lc, 
   }
 }
 
-// volume-weighted mean of the 8 level-(L+1) cells under cell G of level L
+// slot of the level-L leaf at block coordinates b (>= 0), -1 coarser, -2 refined
+__device__ __forceinline__ int lookup_block(const KParams &kp, int member, int L, const int *b) {
+  const long long off = kp.lmap_off[member * (MAXLEV + 1) + L];
+  const int n1 = kp.nbase[1] << (L - 1), n2 = kp.nbase[2] << (L - 1);
+  return kp.lmap[off + ((long long)b[0] * n1 + b[1]) * n2 + b[2]];
+}
+
+// volume-weighted mean of the 8 level-(L+1) cells under the level-L cell at
+// padded index q of the level-L block b (global cell G); same arithmetic and
+// order as the oracle's restriction
 template <typename real>
-__device__ bool restrict_value(const KParams &kp, const real *U, int member, int L, const int *G, real *out) {
+__device__ bool restrict_in_block(const KParams &kp, const real *U, int member, int L, const int *b, const int *q,
+                                  const int *G, real *out) {
   const LevelGeo<real> &F = GeoSel<real>::get(kp.geo, L + 1);
   real sum[NVAR];
 #pragma unroll
   for (int v = 0; v < NVAR; v++) sum[v] = real(0);
   real vs = real(0);
   for (int c = 0; c < 8; c++) {
-    int f[3] = {2 * G[0] + ((c >> 2) & 1), 2 * G[1] + ((c >> 1) & 1), 2 * G[2] + (c & 1)};
-    const int fs = lookup(kp, member, L + 1, f);
-    if (fs < 0) return false;
-    const DevBlock FB = kp.blk[fs];
-    const real V = F.dr3[f[0] + NGH] * F.dcos[f[1] + NGH] * F.dphi;
-    const int q0 = f[0] - FB.ix[0] * kp.nb[0] + NGH, q1 = f[1] - FB.ix[1] * kp.nb[1] + NGH,
-              q2 = f[2] - FB.ix[2] * kp.nb[2] + NGH;
+    const int cb[3] = {(c >> 2) & 1, (c >> 1) & 1, c & 1};
+    int fb[3], fq[3];
 #pragma unroll
-    for (int v = 0; v < NVAR; v++) sum[v] += V * U[cell_index<real>(kp, fs, v, q0, q1, q2)];
+    for (int d = 0; d < 3; d++) {
+      const int l = 2 * (q[d] - NGH) + cb[d];   // 0 .. 2 nb - 1 within the two fine blocks
+      const int hi = l >= kp.nb[d] ? 1 : 0;
+      fb[d] = 2 * b[d] + hi;
+      fq[d] = l - hi * kp.nb[d] + NGH;
+    }
+    const int fs = lookup_block(kp, member, L + 1, fb);
+    if (fs < 0) return false;
+    const int f0 = 2 * G[0] + cb[0], f1 = 2 * G[1] + cb[1];
+    const real V = F.dr3[f0 + NGH] * F.dcos[f1 + NGH] * F.dphi;
+#pragma unroll
+    for (int v = 0; v < NVAR; v++) sum[v] += V * U[cell_index<real>(kp, fs, v, fq[0], fq[1], fq[2])];
     vs += V;
   }
 #pragma unroll
@@ -113,47 +129,61 @@ __device__ bool restrict_value(const KParams &kp, const real *U, int member, int
   return true;
 }
 
+// Same-level copy, prolongation or restriction into the ghost cells of the
+// level-L leaves.  The shell list holds the padded (p0, p1, p2) of a block's
+// ghost cells packed as p0 << 20 | p1 << 10 | p2; the neighbouring block and
+// the cell's index inside it follow from which side of the interior the
+// ghost lies on (no divisions).
 template <typename real>
 __global__ void k_ghost_neighbour(const KParams kp, real *U, const int *list, const int *shell, int nshell,
                                   int L) {
   const int s = blockIdx.y * blockDim.x + threadIdx.x;
   if (s >= nshell) return;
   const int slot = list[blockIdx.x];
-  const DevBlock B = kp.blk[slot];
-  const int lin = shell[s];
-  const int p2 = lin % kp.P[2], p1 = (lin / kp.P[2]) % kp.P[1], p0 = lin / (kp.P[2] * kp.P[1]);
-  const int p[3] = {p0, p1, p2};
-  int G[3];
+  const int member = kp.blk[slot].member;
+  const int code = shell[s];
+  const int p[3] = {code >> 20, (code >> 10) & 1023, code & 1023};
+  int b[3], q[3], G[3];
 #pragma unroll
   for (int d = 0; d < 3; d++) {
-    bool in;
-    G[d] = wrap_dim(kp, L, d, B.ix[d] * kp.nb[d] + p[d] - NGH, in);
-    if (!in) return;  // physical boundary pass fills it
+    const int nb = kp.nb[d];
+    const int side = p[d] < NGH ? -1 : (p[d] >= NGH + nb ? 1 : 0);
+    const int nbl = kp.nbase[d] << (L - 1);
+    int bd = kp.blk[slot].ix[d] + side;
+    if (bd < 0 || bd >= nbl) {
+      if (kp.bc_lo[d] != 0) return;  // physical boundary pass fills it
+      bd += bd < 0 ? nbl : -nbl;     // periodic
+    }
+    b[d] = bd;
+    q[d] = p[d] - side * nb;          // padded index inside block b
+    G[d] = bd * nb + q[d] - NGH;      // global cell at level L
   }
   real val[NVAR];
-  const int o = lookup(kp, B.member, L, G);
+  const int o = lookup_block(kp, member, L, b);
   if (o >= 0) {
-    const DevBlock O = kp.blk[o];
 #pragma unroll
-    for (int v = 0; v < NVAR; v++)
-      val[v] = U[cell_index<real>(kp, o, v, G[0] - O.ix[0] * kp.nb[0] + NGH, G[1] - O.ix[1] * kp.nb[1] + NGH,
-                                  G[2] - O.ix[2] * kp.nb[2] + NGH)];
+    for (int v = 0; v < NVAR; v++) val[v] = U[cell_index<real>(kp, o, v, q[0], q[1], q[2])];
   } else if (o == -1) {
-    int Ic[3] = {G[0] >> 1, G[1] >> 1, G[2] >> 1};
-    const int cs = lookup(kp, B.member, L - 1, Ic);
+    int cb[3], Ic[3];
+#pragma unroll
+    for (int d = 0; d < 3; d++) {
+      cb[d] = b[d] >> 1;
+      Ic[d] = G[d] >> 1;
+    }
+    const int cs = lookup_block(kp, member, L - 1, cb);
     if (cs < 0) {
       atomicOr(kp.status, ST_NAN);
       return;
     }
     prolong_value<real>(kp, U, cs, L - 1, Ic, ((G[0] & 1) << 2) | ((G[1] & 1) << 1) | (G[2] & 1), val);
   } else {
-    if (!restrict_value<real>(kp, U, B.member, L, G, val)) {
+    if (!restrict_in_block<real>(kp, U, member, L, b, q, G, val)) {
       atomicOr(kp.status, ST_NAN);
       return;
     }
   }
 #pragma unroll
-  for (int v = 0; v < NVAR; v++) U[cell_index<real>(kp, slot, v, p0, p1, p2)] = val[v];
+  for (int v = 0; v < NVAR; v++) U[cell_index<real>(kp, slot, v, p[0], p[1], p[2])] = val[v];
 }
 
 // inner boundary state (FP64): map of the containing base cell, cone CME overlay

@@ -37,7 +37,7 @@ EXPORTS = [
     "icarus_profile", "icarus_profile_read", "icarus_set_fp64_islands", "icarus_conservation_sums_static",
     "icarus_mlp_set_params", "icarus_mlp_get_params", "icarus_mlp_features", "icarus_mlp_predict_leaves",
     "icarus_mlp_predict", "icarus_mlp_grad", "icarus_mlp_dataset_clear", "icarus_mlp_dataset_add",
-    "icarus_mlp_train", "icarus_cell_updates", "icarus_destroy",
+    "icarus_mlp_train", "icarus_cell_updates", "icarus_save", "icarus_load", "icarus_destroy",
     "icarus_status_string",
 ]
 
@@ -300,6 +300,19 @@ class Icarus:
         n = C.c_int(0)
         _chk("icarus_kernels_per_step", self.lib.icarus_kernels_per_step(self.ctx, C.byref(n)))
         return n.value
+
+    def save(self, path):
+        """Checkpoint the context to a host file (see icarus_save)."""
+        f = self.lib.icarus_save
+        f.restype, f.argtypes = C.c_int, [C.c_void_p, C.c_char_p]
+        _chk("icarus_save", f(self.ctx, os.fsencode(path)))
+
+    def load(self, path):
+        """Resume from a checkpoint written by a context with the same
+        descriptor (see icarus_load)."""
+        f = self.lib.icarus_load
+        f.restype, f.argtypes = C.c_int, [C.c_void_p, C.c_char_p]
+        _chk("icarus_load", f(self.ctx, os.fsencode(path)))
 
     def profile(self, enable=True):
         _chk("icarus_profile", self.lib.icarus_profile(self.ctx, int(bool(enable))))

@@ -116,3 +116,37 @@ def step_profile(g, n_steps=20, crit=None, repeats=3):
         t_regrid += w2 - w1
     return {"kernels_ms_per_step": tot / n_steps, "kernels": kinds, "leaves": g.n_leaves(-1),
             "flag_ms": 1e3 * t_flag / repeats, "regrid_ms": 1e3 * t_regrid / repeats}
+
+
+def run_learned_window(g, *, n_regrids, regrid_every, max_level, crit=None, t_stop=np.inf):
+    """Advance with the learned pre-flags applied at every regrid and, for the
+    same states, record the plain estimator's flags; returns per-regrid
+    records and the missed-flag rates of the learned and of the plain
+    pre-flags against the next regrid's plain refinements (refinable leaves
+    only: below `max_level`)."""
+    from .icarus import FLAG_LEARNED, FLAG_PLAIN
+    crit = dict(crit or CRIT)
+    recs, steps = [], 0
+    w0 = time.perf_counter()
+    for _ in range(n_regrids):
+        u0 = g.cell_updates()
+        g.step(regrid_every, t_stop=t_stop)
+        steps += regrid_every
+        n0 = g.n_leaves(0)
+        plain = g.flag_refine(**crit, mode=FLAG_PLAIN)[:n0].copy()
+        learned = g.flag_refine(**crit, mode=FLAG_LEARNED)[:n0].copy()   # stays set for the regrid
+        recs.append({"tree": g.tree(0), "plain": plain, "learned": learned, "leaves": g.n_leaves(-1)})
+        g.regrid()
+    wall = time.perf_counter() - w0
+    mp, ml = [], []
+    for a, b in zip(recs[:-1], recs[1:]):
+        x = H.missed_flag_rate(a["tree"], a["plain"] > 0, b["tree"], b["plain"], max_level)
+        y = H.missed_flag_rate(a["tree"], a["learned"] > 0, b["tree"], b["plain"], max_level)
+        if x is not None:
+            mp.append(x)
+            ml.append(y)
+    return {"regrids": n_regrids, "regrid_every": regrid_every, "wall_s": wall,
+            "leaves": [r["leaves"] for r in recs],
+            "extra_preflags": int(sum(int((r["learned"] > 0).sum() - (r["plain"] > 0).sum()) for r in recs)),
+            "missed_refinable_plain": float(np.mean(mp)) if mp else None,
+            "missed_refinable_learned": float(np.mean(ml)) if ml else None, "judged_regrids": len(mp)}
