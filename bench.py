@@ -65,7 +65,7 @@ def parse():
     p.add_argument("--islands", default="0.002,0.1",
                    help="FP32 mode: FP64 pressure where p < a*e or p < b*B^2/2 ('a,b')")
     p.add_argument("--tile", default="", help="force the stage tile 'tile_theta,tile_phi,r_segment'")
-    p.add_argument("--workload", default="wedge", choices=["wedge", "amr", "ensemble", "tt1au", "learned5"],
+    p.add_argument("--workload", default="wedge", choices=["wedge", "amr", "ensemble", "tt1au", "learned5", "series"],
                    help="amr / ensemble / tt1au: stretched AMR CME runs (one JSON line of their own)")
     p.add_argument("--members", type=int, default=32)
     p.add_argument("--max-blocks", type=int, default=60000)
@@ -243,9 +243,9 @@ def run_amr_workload(args):
     ups0 = float(np.sum(g.cell_updates()))
     res = WL.run_cme(g, [cme], t_inj=t_inj, hours_after=args.hours, regrid_every=args.regrid_every)
     rep = WL.amr_report(g, res, wall_relax, t_inj, ups0)
-    rep["profile_at_end"] = WL.step_profile(g)
     line = {"workload": "amr264x36x96_L%d" % args.max_level, "precision": args.precision, **rep}
     print(json.dumps(line), flush=True)
+    print(json.dumps({"workload": line["workload"], "profile_at_end": WL.step_profile(g)}), flush=True)
     return 0
 
 
@@ -262,12 +262,14 @@ def run_ensemble_workload(args):
     t_inj, wall_relax = WL.relax(g, args.relax_days)
     ups0 = float(np.sum(g.cell_updates()))
     res = WL.run_cme(g, draws, t_inj=t_inj, hours_after=args.hours, regrid_every=args.regrid_every,
-                     max_levels=[d["max_level"] for d in draws], stop_hours_after_arrival=6.0)
+                     max_levels=[d["max_level"] for d in draws], stop_hours_after_arrival=6.0,
+                     progress=sys.stderr)
     rep = WL.amr_report(g, res, wall_relax, t_inj, ups0)
-    rep["profile_at_end"] = WL.step_profile(g)
-    print(json.dumps({"workload": f"ensemble{args.members}_amr264x36x96", "precision": "fp32",
-                      "hours_after_injection": args.hours, "max_levels": [d["max_level"] for d in draws], **rep}),
-          flush=True)
+    name = f"ensemble{args.members}_amr264x36x96"
+    print(json.dumps({"workload": name, "precision": "fp32", "hours_after_injection": args.hours,
+                      "max_levels": [d["max_level"] for d in draws],
+                      "speeds_kms": [d["v"] * 100.0 for d in draws], **rep}), flush=True)
+    print(json.dumps({"workload": name, "profile_at_end": WL.step_profile(g)}), flush=True)
     return 0
 
 
@@ -394,6 +396,53 @@ def run_learned5_workload(args):
     return 0
 
 
+def run_series_workload(args):
+    """The 512x60x180 wedge in FP64 and in FP32: relax the wind, inject the
+    cone CME, probe at Earth every 10 minutes for `--hours`; reports both
+    runs' arrival, shock width and peak speed, their wall clocks and the
+    FP32 - FP64 difference per probed variable (the FP64 path is the oracle's
+    arithmetic on the GPU: it matches the CPU oracle to 1e-10, which is too
+    slow for this size)."""
+    import torch
+    from paper_2211_12867_gb300 import harness as H
+    from paper_2211_12867_gb300.icarus import FP32_MIXED, FP64, Icarus
+    torch.cuda.set_device(0)
+    names = ["rho", "v_r", "v_theta", "v_phi", "p", "B_r", "B_theta", "B_phi"]
+    out, series = {}, {}
+    for tag, prec in (("fp32", FP32_MIXED), ("fp64", FP64)):
+        g = Icarus(n_cells=N_CELLS, block=BLOCK, x_min=X_MIN, x_max=X_MAX, omega=I.OMEGA, cfl=0.8, divb_cd=0.8,
+                   precision=prec)
+        wm = I.wind_map(N_CELLS[1], N_CELLS[2], X_MIN[1], X_MAX[1], seed=0, r_in=X_MIN[0])
+        g.set_inner_boundary(0, wm)
+        rc = I.radial_centres(N_CELLS[0], X_MIN[0], X_MAX[0], 0)
+        G = I.initial_prim(wm, rc, X_MIN[0], 1.5, colat_min=X_MIN[1], colat_max=X_MAX[1])
+        g.set_state(0, I.global_to_blocks(G, g.tree(0), BLOCK), prim=True)
+        t_end = I.days(args.relax_days)
+        w0 = time.perf_counter()
+        while g.step(2000, t_stop=t_end)[0] < t_end:
+            pass
+        wall_relax = time.perf_counter() - w0
+        ups0 = float(np.sum(g.cell_updates()))
+        res = H.propagate(g, [I.cme_config2(seed=0)], t_inj=t_end, duration=I.hours(args.hours))
+        ups = float(np.sum(g.cell_updates())) - ups0
+        to_h = lambda x: None if x is None else x / I.hours(1.0)
+        out[tag] = {"arrival_h": to_h(None if res.arrival[0] is None else res.arrival[0] - t_end),
+                    "shock_width_h": to_h(res.width[0]), "peak_speed_kms": None if res.peak[0] is None else
+                    res.peak[0] * 100.0, "wall_s": res.wall_s, "relax_wall_s": wall_relax, "steps": res.steps,
+                    "cell_updates_per_s": ups / res.wall_s, "time_to_arrival_s": res.wall_to(res.arrival[0])}
+        series[tag] = res.series[0]
+        del g
+    a, b = series["fp32"], series["fp64"]
+    diff = {n: {"max_abs": float(np.max(np.abs(a[:, v] - b[:, v]))),
+                "max_rel_to_range": float(np.max(np.abs(a[:, v] - b[:, v])) / max(np.ptp(b[:, v]), 1e-300))}
+            for v, n in enumerate(names)}
+    a32, a64 = out["fp32"]["arrival_h"], out["fp64"]["arrival_h"]
+    print(json.dumps({"workload": WORKLOAD + "_series", "hours_after_injection": args.hours,
+                      "relax_days": args.relax_days, **out, "fp32_minus_fp64_at_earth": diff,
+                      "arrival_diff_h": None if a32 is None or a64 is None else abs(a32 - a64)}), flush=True)
+    return 0
+
+
 def main():
     args = parse()
     if args.impl == "reference":
@@ -406,6 +455,8 @@ def main():
         return run_tt1au_workload(args)
     if args.workload == "learned5":
         return run_learned5_workload(args)
+    if args.workload == "series":
+        return run_series_workload(args)
     import torch
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))

@@ -12,7 +12,7 @@ import itertools
 
 import numpy as np
 
-TILES = [(8, 32), (4, 32), (12, 20), (6, 36), (12, 12), (8, 8)]
+TILES = [(8, 32), (4, 32), (12, 20), (10, 24), (8, 24), (6, 36), (12, 12), (8, 8)]
 
 
 def candidates(block):

@@ -84,9 +84,21 @@ __global__ void k_estimator(const KParams kp, const real *U, int slot0, double e
   const size_t nbc = (size_t)kp.n_base_cells[0] * kp.n_base_cells[1] * kp.n_base_cells[2];
   const double *vbg = kp.vbg + (size_t)B.member * nbc;
   int refine = 0, keep = 0;
-  for (int c = threadIdx.x; c < kp.icells; c += blockDim.x) {
+  // without a recorded background the gate is closed everywhere: no cell
+  // counts and the block is flagged for coarsening
+  for (int c = has_bg ? threadIdx.x : kp.icells; c < kp.icells; c += blockDim.x) {
     const int k = c % kp.nb[2], j = (c / kp.nb[2]) % kp.nb[1], i = c / (kp.nb[2] * kp.nb[1]);
     const int p0 = i + NGH, p1 = j + NGH, p2 = k + NGH;
+    // the speed gate first: E only matters where it is open, and not at all
+    // once this thread has found a refining cell (the flags are unchanged)
+    const double r0 = (double)U[cidx<real>(kp, slot, 0, p0, p1, p2)];
+    const double m0 = (double)U[cidx<real>(kp, slot, 1, p0, p1, p2)];
+    {
+      const int I = B.ix[0] * kp.nb[0] + i, J = B.ix[1] * kp.nb[1] + j, K = B.ix[2] * kp.nb[2] + k;
+      const double vb = vbg[((size_t)(I >> sh) * kp.n_base_cells[1] + (J >> sh)) * kp.n_base_cells[2] + (K >> sh)];
+      const double vr = __ddiv_rn(m0, r0);
+      if (!(vr > __dadd_rn(vb, dv)) || refine) continue;
+    }
     double u0[NVAR];
 #pragma unroll
     for (int v = 0; v < NVAR; v++) u0[v] = (double)U[cidx<real>(kp, slot, v, p0, p1, p2)];
@@ -109,15 +121,8 @@ __global__ void k_estimator(const KParams kp, const real *U, int slot0, double e
     const double er = loehner(rm, u0[0], rp, eps);
     const double ep = loehner(pm, est_pressure(u0, kp.gamma), pp, eps);
     const double E = er > ep ? er : ep;
-    bool gate = false;
-    if (has_bg) {
-      const int I = B.ix[0] * kp.nb[0] + i, J = B.ix[1] * kp.nb[1] + j, K = B.ix[2] * kp.nb[2] + k;
-      const double vb = vbg[((size_t)(I >> sh) * kp.n_base_cells[1] + (J >> sh)) * kp.n_base_cells[2] + (K >> sh)];
-      const double vr = __ddiv_rn(u0[1], u0[0]);
-      gate = vr > __dadd_rn(vb, dv);
-    }
-    if (gate && E > e_ref) refine = 1;
-    if (gate && E > e_crs) keep = 1;
+    if (E > e_ref) refine = 1;
+    if (E > e_crs) keep = 1;
   }
   refine = __syncthreads_or(refine);
   keep = __syncthreads_or(keep);

@@ -184,26 +184,26 @@ __global__ void __launch_bounds__(stage_threads(TJ, TK), stage_min_ctas(sizeof(r
     const bool valid = tid < TJ * TK && jl < nvj && kl < nvk;
     const int j = j0 + jl, k = k0 + kl;           // interior indices in the block
 
-    // Planes of U_in are copied asynchronously (cp.async, 2 cells x 8
-    // variables per unit) straight into their ring slot and converted to
-    // primitives in place one iteration later, by the thread that copied them
-    // (no barrier between copy and conversion).  Units go to the highest
+    // Planes of U_in are copied asynchronously (cp.async, 4 bytes per copy)
+    // straight into their ring slot and converted to primitives in place one
+    // iteration later, by the thread that copied them (no barrier between
+    // copy and conversion).  A unit is two cells half a plane apart, so the
+    // threads of a warp write consecutive cells.  Units go to the highest
     // thread indices, which own no second div B position.
-    constexpr int HK = RK / 2, NU = RJ * HK;
+    constexpr int NU = RP / 2;
     auto slotp = [&](int p) -> real * { return ring + ((p + 5) % 5) * NVAR * RP; };
     auto issue_plane = [&](int p) {
       real *dst = slotp(p);
       const real *src = Uin + (size_t)(p + NGH) * plane;
       for (int u = NT - 1 - tid; u < NU; u += NT) {
-        const int jj = u / HK, kk = 2 * (u - (u / HK) * HK);
-        const int pj = j0 + jj, pk = k0 + kk;
-        if (pj < P1 && pk < P2) {
-          const int q = jj * RK + kk;
 #pragma unroll
-          for (int v = 0; v < NVAR; v++) {
-            const real *g = src + v * vstride + (size_t)pj * P2 + pk;
-            cp_async<sizeof(real)>(&el<real, RP>(dst, v, q), g);
-            cp_async<sizeof(real)>(&el<real, RP>(dst, v, q + 1), g + 1);
+        for (int h = 0; h < 2; h++) {
+          const int q = u + h * NU, jj = q / RK, kk = q - (q / RK) * RK;
+          const int pj = j0 + jj, pk = k0 + kk;
+          if (pj < P1 && pk < P2) {
+#pragma unroll
+            for (int v = 0; v < NVAR; v++)
+              cp_async<sizeof(real)>(&el<real, RP>(dst, v, q), src + v * vstride + (size_t)pj * P2 + pk);
           }
         }
       }
@@ -212,11 +212,10 @@ __global__ void __launch_bounds__(stage_threads(TJ, TK), stage_min_ctas(sizeof(r
     auto convert_plane = [&](int p) {
       real *pl = slotp(p);
       for (int u = NT - 1 - tid; u < NU; u += NT) {
-        const int jj = u / HK, kk = 2 * (u - (u / HK) * HK);
-        if (j0 + jj < P1 && k0 + kk < P2) {
 #pragma unroll
-          for (int h = 0; h < 2; h++) {
-            const int q = jj * RK + kk + h;
+        for (int h = 0; h < 2; h++) {
+          const int q = u + h * NU, jj = q / RK, kk = q - (q / RK) * RK;
+          if (j0 + jj < P1 && k0 + kk < P2) {
             real uu[NVAR], wv[NVAR];
             ld8<real, RP>(pl, q, uu);
             cons2prim<real>(uu, wv, gamma, pfl, isl);
@@ -365,7 +364,11 @@ __global__ void __launch_bounds__(stage_threads(TJ, TK), stage_min_ctas(sizeof(r
               st8<real, NTH>(fthb, row * TK + col, F);
             }
           } else {
-            const int g = f - NTH, row = g / (TK + 1), col = g - (g / (TK + 1)) * (TK + 1);
+            // phi faces: the first TJ * TK in rows of TK (a warp's quarters stay
+            // in one row when TK is a multiple of 8), then the last column
+            const int g = f - NTH;
+            const int row = g < TJ * TK ? g / TK : g - TJ * TK;
+            const int col = g < TJ * TK ? g - (g / TK) * TK : TK;
             if (row < nvj && col <= nvk) {
               gather(pl, row + 2, col, a);
               gather(pl, row + 2, col + 1, b);
@@ -564,6 +567,8 @@ int dispatch(const KParams &kp, const StageLaunch &sl, cudaStream_t s) {
   if (sl.tile_j == 4 && sl.tile_k == 32) return launch_t<real, 4, 32>(kp, sl, s);
   if (sl.tile_j == 12 && sl.tile_k == 20) return launch_t<real, 12, 20>(kp, sl, s);
   if (sl.tile_j == 6 && sl.tile_k == 36) return launch_t<real, 6, 36>(kp, sl, s);
+  if (sl.tile_j == 10 && sl.tile_k == 24) return launch_t<real, 10, 24>(kp, sl, s);
+  if (sl.tile_j == 8 && sl.tile_k == 24) return launch_t<real, 8, 24>(kp, sl, s);
   return -2;
 }
 
@@ -586,6 +591,8 @@ int occupancy(int tj, int tk) {
   if (tj == 4 && tk == 32) return occupancy_t<real, 4, 32>();
   if (tj == 12 && tk == 20) return occupancy_t<real, 12, 20>();
   if (tj == 6 && tk == 36) return occupancy_t<real, 6, 36>();
+  if (tj == 10 && tk == 24) return occupancy_t<real, 10, 24>();
+  if (tj == 8 && tk == 24) return occupancy_t<real, 8, 24>();
   return 1;
 }
 
@@ -598,7 +605,8 @@ size_t stage_smem_bytes(int precision, int tj, int tk) {
 // an instantiated tile whose shared memory fits one CTA on this device
 int stage_tile_supported(int precision, int tj, int tk) {
   const bool known = (tj == 8 && tk == 8) || (tj == 12 && tk == 12) || (tj == 8 && tk == 32) ||
-                     (tj == 4 && tk == 32) || (tj == 12 && tk == 20) || (tj == 6 && tk == 36);
+                     (tj == 4 && tk == 32) || (tj == 12 && tk == 20) || (tj == 6 && tk == 36) ||
+                     (tj == 10 && tk == 24) || (tj == 8 && tk == 24);
   if (!known) return 0;
   int dev = 0, lim = 0;
   if (cudaGetDevice(&dev) != cudaSuccess ||

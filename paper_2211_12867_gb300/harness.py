@@ -242,12 +242,12 @@ def advance_to(g, t_target, max_steps=1_000_000, regrid_every=0, crit=None, coun
 
 
 def propagate(g, cmes, *, t_inj, duration, sample=None, earth_lon0=math.pi, regrid_every=0, crit=None,
-              on_regrid=None, stop_after_arrival=None):
+              on_regrid=None, stop_after_arrival=None, progress=None):
     """Inject one cone CME per member at t_inj and record Earth time series
     every `sample` (default 10 min) for `duration`; returns RunResult.  With
     `stop_after_arrival` (code time), a member stops advancing once its shock
     has arrived and that much time has passed (its later samples repeat the
-    last state)."""
+    last state).  `progress` (a file) receives one line per simulated hour."""
     import time as _time
     sample = I.hours(1.0 / 6.0) if sample is None else sample
     nm = g.n_members
@@ -274,6 +274,9 @@ def propagate(g, cmes, *, t_inj, duration, sample=None, earth_lon0=math.pi, regr
                 if a is not None and times[k] >= a + stop_after_arrival:
                     t_hold[m] = times[k]
         wall_at[k] = _time.perf_counter() - w0
+        if progress is not None and int((times[k] - t_inj) / I.hours(1.0)) > int((times[k - 1] - t_inj) / I.hours(1.0)):
+            print(f"t = {(times[k] - t_inj) / I.hours(1.0):.1f} h  wall {wall_at[k]:.1f} s  leaves {g.n_leaves(-1)}  "
+                  f"held {int(np.sum(np.isfinite(t_hold)))}/{nm}", file=progress, flush=True)
     wall = wall_at[-1]
     arr = [arrival_time(times, series[m, :, 1], bg[m, :, 1]) for m in range(nm)]
     wid = [shock_width(times, series[m, :, 1], a) for m, a in zip(range(nm), arr)]

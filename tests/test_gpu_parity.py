@@ -60,7 +60,7 @@ def test_ragged_tiles_and_segments():
     """blocks that the (theta, phi) tile and the radial segment do not divide"""
     g, o = make_pair(n=(40, 20, 24), nb=(20, 10, 12))
     wind_setup(g, o)
-    for tile, seg in (((8, 8), 6), ((4, 32), 7), ((12, 12), 0), ((6, 36), 3), ((12, 20), 5)):
+    for tile, seg in (((8, 8), 6), ((4, 32), 7), ((12, 12), 0), ((6, 36), 3), ((12, 20), 5), ((10, 24), 7)):
         g2, o2 = make_pair(n=(40, 20, 24), nb=(20, 10, 12))
         wind_setup(g2, o2)
         g2.set_tile(*tile, seg)
