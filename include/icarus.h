@@ -153,8 +153,10 @@ icarus_status icarus_inject_cone_cme(icarus_ctx *ctx, int member, const icarus_c
  * predictor-corrector (each step: ghost fill, half step, ghost fill, full
  * step with parabolic cleaning, reflux at coarse-fine faces, CFL time step).
  * t_stop[n_members] (host): a member's dt is clipped so that it lands on
- * t_stop, after which it stops.  t_out[n_members] (host, may be NULL)
- * receives the members' times; passing it synchronises the stream. */
+ * t_stop, after which it stops.  When every t_stop is finite the call reads
+ * the members' times back every 8 steps (synchronising) and returns early
+ * once all have landed.  t_out[n_members] (host, may be NULL) receives the
+ * members' times; passing it synchronises the stream. */
 icarus_status icarus_step(icarus_ctx *ctx, int n_steps, const double *t_stop, double *t_out);
 
 /* Evaluate the refinement criterion on every leaf of every member (after a

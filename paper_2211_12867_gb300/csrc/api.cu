@@ -238,6 +238,7 @@ struct icarus_ctx {
   cudaGraphExec_t graph = nullptr;
   bool graph_valid = false;
   bool poisoned = false;
+  bool ghosts_fresh = false;   // ghosts of U filled for the current state and time
   std::vector<double> h_tstop;
   int kernels_per_step = 0;
   // learned pre-flagger
@@ -1006,6 +1007,7 @@ void icarus_destroy(icarus_ctx *c) {
 
 icarus_status icarus_set_inner_boundary(icarus_ctx *c, int member, const double *prim) {
   if (!member_ok(c, member) || !prim) return ICARUS_ERR_ARG;
+  c->ghosts_fresh = false;
   if (c->poisoned) return ICARUS_ERR_STATE;
   const size_t n = (size_t)NVAR * c->d.n_cells[1] * c->d.n_cells[2];
   CK(cudaMemcpyAsync(c->bmap + member * n, prim, n * sizeof(double), cudaMemcpyHostToDevice, c->stream));
@@ -1016,6 +1018,7 @@ icarus_status icarus_set_inner_boundary(icarus_ctx *c, int member, const double 
 
 icarus_status icarus_inject_cone_cme(icarus_ctx *c, int member, const icarus_cone *p) {
   if (!member_ok(c, member) || !p) return ICARUS_ERR_ARG;
+  c->ghosts_fresh = false;
   if (c->poisoned) return ICARUS_ERR_STATE;
   if (!(p->v > 0.0) || !(p->half_width > 0.0) || !(p->half_width < M_PI / 2) || !(p->rho > 0.0) || !(p->p > 0.0))
     return ICARUS_ERR_ARG;
@@ -1045,6 +1048,7 @@ icarus_status icarus_inject_cone_cme(icarus_ctx *c, int member, const icarus_con
 
 icarus_status icarus_set_time(icarus_ctx *c, int member, double t) {
   if (!member_ok(c, member)) return ICARUS_ERR_ARG;
+  c->ghosts_fresh = false;
   CK(cudaMemcpyAsync(c->t + member, &t, sizeof(double), cudaMemcpyHostToDevice, c->stream));
   CK(cudaStreamSynchronize(c->stream));
   return ICARUS_OK;
@@ -1100,6 +1104,7 @@ icarus_status icarus_kernels_per_step(icarus_ctx *c, int *n) {
 
 icarus_status icarus_step(icarus_ctx *c, int n_steps, const double *t_stop, double *t_out) {
   if (!c || n_steps < 0 || !t_stop) return ICARUS_ERR_ARG;
+  c->ghosts_fresh = false;
   if (c->poisoned) return ICARUS_ERR_STATE;
   const int nm = c->d.n_members;
   c->h_tstop.assign(t_stop, t_stop + nm);
@@ -1127,10 +1132,29 @@ icarus_status icarus_step(icarus_ctx *c, int n_steps, const double *t_stop, doub
         }
         c->graph_valid = true;
       }
-      for (int s = 0; s < n_steps; s++) CK(cudaGraphLaunch(c->graph, c->stream));
-    } else {
-      for (int s = 0; s < n_steps; s++) c->kernels_per_step = enqueue_step(c);
-      CK(cudaPeekAtLastError());
+    }
+    // When every member has a finite stop time, the members' times are read
+    // back every STEP_CHUNK steps and the call returns once all have landed
+    // (the remaining steps would launch work for nobody).
+    bool bounded = true;
+    for (int m = 0; m < nm; m++) bounded = bounded && std::isfinite(c->h_tstop[m]);
+    constexpr int STEP_CHUNK = 8;
+    std::vector<double> th(nm);
+    for (int s0 = 0; s0 < n_steps; s0 += STEP_CHUNK) {
+      const int ns = std::min(STEP_CHUNK, n_steps - s0);
+      if (c->graph_valid && c->use_graph && !c->prof_on && c->stream != nullptr) {
+        for (int s = 0; s < ns; s++) CK(cudaGraphLaunch(c->graph, c->stream));
+      } else {
+        for (int s = 0; s < ns; s++) c->kernels_per_step = enqueue_step(c);
+        CK(cudaPeekAtLastError());
+      }
+      if (bounded && s0 + ns < n_steps) {
+        CK(cudaMemcpyAsync(th.data(), c->t, sizeof(double) * nm, cudaMemcpyDeviceToHost, c->stream));
+        CK(cudaStreamSynchronize(c->stream));
+        bool done = true;
+        for (int m = 0; m < nm; m++) done = done && th[m] >= c->h_tstop[m];
+        if (done) break;
+      }
     }
   }
   // the host copy of t_stop stays alive in the context until the next call
@@ -1176,6 +1200,7 @@ icarus_status icarus_get_tree(icarus_ctx *c, int member, int32_t *rows, int capa
 
 icarus_status icarus_set_state(icarus_ctx *c, int member, const double *host, size_t n, int is_prim) {
   if (!member_ok(c, member) || !host) return ICARUS_ERR_ARG;
+  c->ghosts_fresh = false;
   if (c->poisoned) return ICARUS_ERR_STATE;
   const size_t per = (size_t)NVAR * c->kp.icells;
   const int nl = (int)c->mem[member].leaves.size();
@@ -1256,7 +1281,11 @@ icarus_status icarus_probe(icarus_ctx *c, int member, int n_pts, const double *r
   if (!member_ok(c, member) || n_pts < 0 || n_pts > 4096 || (n_pts && (!rtp || !prim_out))) return ICARUS_ERR_ARG;
   if (c->poisoned) return ICARUS_ERR_STATE;
   if (!n_pts) return ICARUS_OK;
-  enqueue_ghost(c, c->U, 0.0);
+  // probes of several members at one time share one ghost fill
+  if (!c->ghosts_fresh) {
+    enqueue_ghost(c, c->U, 0.0);
+    c->ghosts_fresh = true;
+  }
   CK(cudaMemcpyAsync(c->probe_in, rtp, sizeof(double) * 3 * n_pts, cudaMemcpyHostToDevice, c->stream));
   probe_launch2(c->kp, c->U, c->prec, member, c->d.max_level, n_pts, c->probe_in, c->probe_out, c->stream);
   CK(cudaPeekAtLastError());
@@ -1293,6 +1322,7 @@ icarus_status icarus_set_flags(icarus_ctx *c, const int8_t *flags) {
 
 icarus_status icarus_regrid(icarus_ctx *c) {
   if (!c) return ICARUS_ERR_ARG;
+  c->ghosts_fresh = false;
   if (c->poisoned) return ICARUS_ERR_STATE;
   if (!c->flags_valid) return ICARUS_ERR_STATE;
   if (c->d.max_level == 1) {
@@ -1436,6 +1466,7 @@ icarus_status icarus_regrid(icarus_ctx *c) {
 
 icarus_status icarus_set_fp64_islands(icarus_ctx *c, double p_over_e, double beta) {
   if (!c || !(p_over_e >= 0.0) || !(beta >= 0.0)) return ICARUS_ERR_ARG;
+  c->ghosts_fresh = false;
   c->isl_pe = p_over_e;
   c->isl_beta = beta;
   fill_kp(c);
@@ -1725,6 +1756,7 @@ icarus_status icarus_save(icarus_ctx *c, const char *path) {
 
 icarus_status icarus_load(icarus_ctx *c, const char *path) {
   if (!c || !path) return ICARUS_ERR_ARG;
+  c->ghosts_fresh = false;
   const int nm = c->d.n_members;
   const size_t nbc = (size_t)c->d.n_cells[0] * c->d.n_cells[1] * c->d.n_cells[2];
   const size_t nbm = (size_t)NVAR * c->d.n_cells[1] * c->d.n_cells[2];
