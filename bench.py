@@ -28,6 +28,7 @@ from __future__ import annotations
 import argparse
 import hashlib
 import json
+import re
 import math
 import os
 import subprocess
@@ -165,18 +166,20 @@ def setup_grid(precision, seed=0):
 
 
 def roofline_traffic(prec_tag):
-    """DRAM traffic per corrector launch from the committed ncu summary, if it
-    was taken on the current stage-kernel source."""
-    path = os.path.join(ROOT, "profiles", "stage_corrector_traffic.json")
+    """DRAM traffic per corrector launch (dram__bytes_read + write) from the
+    committed ncu summary, if it was taken on the current stage-kernel
+    source and precision; None otherwise."""
+    path = os.path.join(ROOT, "profiles", f"k_stage_corrector_wedge512_{'fp32' if prec_tag == 'f32' else 'fp64'}.md")
     src = os.path.join(ROOT, "paper_2211_12867_gb300", "csrc", "k_stage.cu")
     try:
-        with open(path) as f:
-            d = json.load(f)
+        text = open(path).read()
         h = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
-        if d.get("k_stage_sha256_16") != h or d.get("precision") != prec_tag:
+        m = re.search(r"sha256\[:16\] = `([0-9a-f]{16})`", text)
+        t = re.search(r"traffic_bytes_per_launch = (\d+)", text)
+        if not m or not t or m.group(1) != h:
             return None
-        return float(d["bytes_per_launch_full_workload"])
-    except Exception:
+        return float(t.group(1))
+    except OSError:
         return None
 
 
