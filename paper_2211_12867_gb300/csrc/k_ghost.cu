@@ -135,7 +135,7 @@ __device__ bool restrict_in_block(const KParams &kp, const real *U, int member, 
 // the cell's index inside it follow from which side of the interior the
 // ghost lies on (no divisions).
 template <typename real>
-__global__ void k_ghost_neighbour(const KParams kp, real *U, const int *list, const int *shell, int nshell,
+__global__ void __launch_bounds__(256, sizeof(real) == 4 ? 4 : 2) k_ghost_neighbour(const KParams kp, real *U, const int *list, const int *shell, int nshell,
                                   int L) {
   const int s = blockIdx.y * blockDim.x + threadIdx.x;
   if (s >= nshell) return;
