@@ -1104,7 +1104,7 @@ icarus_status icarus_kernels_per_step(icarus_ctx *c, int *n) {
 
 icarus_status icarus_step(icarus_ctx *c, int n_steps, const double *t_stop, double *t_out) {
   if (!c || n_steps < 0 || !t_stop) return ICARUS_ERR_ARG;
-  c->ghosts_fresh = false;
+  if (n_steps > 0) c->ghosts_fresh = false;
   if (c->poisoned) return ICARUS_ERR_STATE;
   const int nm = c->d.n_members;
   c->h_tstop.assign(t_stop, t_stop + nm);
@@ -1171,6 +1171,7 @@ icarus_status icarus_ghost_fill(icarus_ctx *c) {
   if (c->poisoned) return ICARUS_ERR_STATE;
   enqueue_ghost(c, c->U, 0.0);
   CK(cudaPeekAtLastError());
+  c->ghosts_fresh = true;
   return ICARUS_OK;
 }
 
@@ -1296,7 +1297,10 @@ icarus_status icarus_probe(icarus_ctx *c, int member, int n_pts, const double *r
 icarus_status icarus_flag_refine(icarus_ctx *c, const icarus_refine *crit, int8_t *flags_out) {
   if (!c || !crit) return ICARUS_ERR_ARG;
   if (c->poisoned) return ICARUS_ERR_STATE;
-  enqueue_ghost(c, c->U, 0.0);
+  if (!c->ghosts_fresh) {
+    enqueue_ghost(c, c->U, 0.0);
+    c->ghosts_fresh = true;
+  }
   estimator_launch(c->kp, c->U, c->prec, 0, c->nleaves, crit->e_refine, crit->e_coarsen, crit->eps, crit->dv,
                    c->flags, c->stream);
   if (crit->mode == ICARUS_FLAG_LEARNED) {
@@ -1322,6 +1326,7 @@ icarus_status icarus_set_flags(icarus_ctx *c, const int8_t *flags) {
 
 icarus_status icarus_regrid(icarus_ctx *c) {
   if (!c) return ICARUS_ERR_ARG;
+  const bool fresh = c->ghosts_fresh;   // e.g. filled by the flagging just before
   c->ghosts_fresh = false;
   if (c->poisoned) return ICARUS_ERR_STATE;
   if (!c->flags_valid) return ICARUS_ERR_STATE;
@@ -1329,8 +1334,8 @@ icarus_status icarus_regrid(icarus_ctx *c) {
     c->flags_valid = false;
     return ICARUS_OK;
   }
-  // fill ghosts of the current state: prolongation reads the parents' halos
-  enqueue_ghost(c, c->U, 0.0);
+  // ghosts of the current state: prolongation reads the parents' halos
+  if (!fresh) enqueue_ghost(c, c->U, 0.0);
   CK(cudaPeekAtLastError());
   std::vector<MoveOp> ops;
   std::vector<Member> next(c->d.n_members);
@@ -1361,13 +1366,20 @@ icarus_status icarus_regrid(icarus_ctx *c) {
         for (int q = 0; q < 8; q++) T[i + q] = l.level - 1;
     }
     // 2:1 balance, least fixed point
-    std::vector<std::vector<int>> nb(n);
-    for (int i = 0; i < n; i++) neighbours(c, M, i, nb[i]);
+    // neighbour lists in one flat array (offsets per leaf)
+    std::vector<int> nb_off(n + 1, 0), nb_all, tmp;
+    nb_all.reserve((size_t)n * 26);
+    for (int i = 0; i < n; i++) {
+      neighbours(c, M, i, tmp);
+      nb_all.insert(nb_all.end(), tmp.begin(), tmp.end());
+      nb_off[i + 1] = (int)nb_all.size();
+    }
     bool changed = true;
     while (changed) {
       changed = false;
       for (int i = 0; i < n; i++) {
-        for (int j : nb[i]) {
+        for (int e = nb_off[i]; e < nb_off[i + 1]; e++) {
+          const int j = nb_all[e];
           if (T[j] > T[i] + 1) {
             if (T[i] < M.leaves[i].level) {
               // cancel the family's coarsening: find child 0 of the family
