@@ -485,18 +485,13 @@ def main():
     if args.workload == "series":
         return run_series_workload(args)
     import torch
-    world = int(os.environ.get("WORLD_SIZE", "1"))
-    rank = int(os.environ.get("RANK", "0"))
-    local = int(os.environ.get("LOCAL_RANK", "0"))
-    dist = None
-    if world > 1:
-        import torch.distributed as dist
-        torch.cuda.set_device(local)
-        dist.init_process_group("nccl")
-    else:
+    from paper_2211_12867_gb300.replicas import ReplicaGroup
+    grp = ReplicaGroup("nccl")
+    world, rank, local = grp.world, grp.rank, grp.local
+    if world == 1:
         torch.cuda.set_device(0)
     prec_tag = "f32" if args.precision == "fp32" else "f64"
-    g, W0, wm, cme = setup_grid(args.precision, seed=rank)
+    g, W0, wm, cme = setup_grid(args.precision, seed=grp.seed)
     from paper_2211_12867_gb300.icarus import set_fp64_islands
     isl = tuple(float(x) for x in args.islands.split(","))
     set_fp64_islands(g, *isl)
@@ -519,8 +514,7 @@ def main():
         return 0
 
     def barrier():
-        if dist is not None:
-            dist.barrier()
+        grp.barrier()
         torch.cuda.synchronize()
 
     # ---- timed region: graph replay ----
@@ -532,12 +526,8 @@ def main():
         e1.record(g.stream)
         e1.synchronize()
     barrier()
-    ms = e0.elapsed_time(e1)
-    if dist is not None:
-        t = torch.tensor([ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
-    value = cells * args.steps * world / (ms / 1e3)
+    ms = grp.max_over_ranks(e0.elapsed_time(e1))
+    value = grp.job_rate(cells * args.steps, ms / 1e3)
     kps = g.kernels_per_step()
 
     # ---- per-kernel durations (direct launches with event pairs) ----
@@ -582,13 +572,9 @@ def main():
     pin_out[...] = g.get_state(0)                   # d2h: the job's output state
     torch.cuda.synchronize()
     barrier()
-    e2e_s = time.perf_counter() - w0
-    if dist is not None:
-        t = torch.tensor([e2e_s], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_s = float(t.item())
+    e2e_s = grp.max_over_ranks(time.perf_counter() - w0)
     state_bytes = W0.size * 8
-    e2e = {"value": cells * args.steps * world / e2e_s, "unit": "cell-updates/s",
+    e2e = {"value": grp.job_rate(cells * args.steps, e2e_s), "unit": "cell-updates/s",
            "h2d_bytes_per_step": (state_bytes + args.steps * (8 + 24)) / args.steps,
            "d2h_bytes_per_step": (state_bytes + args.steps * (8 + 64)) / args.steps}
 
@@ -609,9 +595,7 @@ def main():
                 "roofline": roofline, "cpu_baseline": cb, "e2e": e2e, "gpu_launches": kps * args.steps,
                 "clocks": clk.summary(), "status_word": word, "floor_hits": floor_hits}
         print(json.dumps(line), flush=True)
-    if dist is not None:
-        dist.barrier()
-        dist.destroy_process_group()
+    grp.close()
     return 0
 
 
