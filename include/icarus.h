@@ -135,33 +135,57 @@ icarus_status icarus_arena_bytes(const icarus_grid_desc *desc, size_t *bytes);
 
 /* Create a context on the caller's arena and stream: geometry tables for all
  * levels, base-level blocks for every member, state zeroed.  *out receives
- * the context (free with icarus_destroy). */
+ * the context (free with icarus_destroy).
+ * Passages: Sect. 2.1 (domain 0.1-2 AU, +-60 deg latitude, 360 deg longitude,
+ * two ghost layers at the boundaries); Sect. 2.2 and Eq. 5 (radial stretching:
+ * a cell's radial width grows in proportion to its radius, so the faces are
+ * geometric); Tables 1 and 3 (resolutions per level); Sect. 3 (every level
+ * halves the cells in all three directions).
+ * Errors: ICARUS_ERR_ARG for an inconsistent descriptor, ICARUS_ERR_ARENA if
+ * arena_bytes is below icarus_arena_bytes or the arena is not 256-byte
+ * aligned, ICARUS_ERR_CUDA if a CUDA call fails; *out is then NULL. */
 icarus_status icarus_init_grid(const icarus_grid_desc *desc, icarus_ctx **out);
 
 /* Inner-boundary primitive map of one member (Sect. 2.1: boundary values
- * constant in time in the co-rotating frame): host FP64 [8][n_theta][n_phi]
- * at the base-level angular cells.  Both inner ghost layers of every level
- * take the value of the containing base cell (not rescaled in r). */
+ * constant in time in the co-rotating frame, two ghost layers): host FP64
+ * [8][n_theta][n_phi] at the base-level angular cells, copied (the caller
+ * keeps its array).  Both inner ghost layers of every level take the value of
+ * the containing base cell (not rescaled in r).  ICARUS_ERR_ARG for a bad
+ * member or a NULL map. */
 icarus_status icarus_set_inner_boundary(icarus_ctx *ctx, int member, const double *prim);
 
-/* Start a cone CME on one member (Eqs. 1-4) and record the member's
- * background radial speed per base cell from the current state (the gate of
- * the refinement criterion).  All leaves of the member must be at level 1. */
+/* Start a cone CME on one member (Sect. 2.1, Eqs. 1-4: the cone's
+ * cross-section with the inner boundary grows and shrinks as the CME sphere
+ * passes through it) and record the member's background radial speed per
+ * base cell from the current state (the gate of the refinement criterion).
+ * cme (host) is copied.  All leaves of the member must be at level 1
+ * (ICARUS_ERR_STATE otherwise). */
 icarus_status icarus_inject_cone_cme(icarus_ctx *ctx, int member, const icarus_cone *cme);
 
 /* Advance every member by up to n_steps steps of the midpoint
  * predictor-corrector (each step: ghost fill, half step, ghost fill, full
  * step with parabolic cleaning, reflux at coarse-fine faces, CFL time step).
+ * Passage: Sect. 2.1 (ideal MHD in the co-rotating frame, TVDLF scheme second
+ * order in space and time with the Woodward limiter, parabolic cleaning of
+ * div B); the refinement levels of Sect. 3 advance with one shared time step.
  * t_stop[n_members] (host): a member's dt is clipped so that it lands on
  * t_stop, after which it stops.  When every t_stop is finite the call reads
  * the members' times back every 8 steps (synchronising) and returns early
  * once all have landed.  t_out[n_members] (host, may be NULL) receives the
- * members' times; passing it synchronises the stream. */
+ * members' times; passing it synchronises the stream.
+ * Errors: the status word (NaN, floor budget, bounded wait) is checked at
+ * every synchronisation of the call.  A call with t_out == NULL and infinite
+ * stop times does not synchronise: it leaves a copy of the status word on
+ * its way to the host, and the next icarus_step reports what it holds
+ * (ICARUS_ERR_NONPHYSICAL or ICARUS_ERR_TIMEOUT) as soon as it has landed. */
 icarus_status icarus_step(icarus_ctx *ctx, int n_steps, const double *t_stop, double *t_out);
 
 /* Evaluate the refinement criterion on every leaf of every member (after a
  * ghost fill at the current time).  flags_out (host, optional): one int8 per
- * leaf in global leaf order (member-major, Morton within a member). */
+ * leaf in global leaf order (member-major, Morton within a member).
+ * Passage: Sect. 3 (refine where the solution meets the criterion, coarsen
+ * again once it no longer does); Sect. 3.2 for ICARUS_FLAG_SHOCK.  The flags
+ * stay on the device for icarus_regrid.  Synchronises when flags_out is set. */
 icarus_status icarus_flag_refine(icarus_ctx *ctx, const icarus_refine *crit, int8_t *flags_out);
 
 /* Replace the current flags (host int8, global leaf order), e.g. to replay a
@@ -172,6 +196,9 @@ icarus_status icarus_set_flags(icarus_ctx *ctx, const int8_t *flags);
  * sibling families all flagged -1 (refinement wins), enforce 2:1 balance over
  * faces, edges and corners (least balanced refinement), prolong new children
  * conservatively, restrict coarsened parents, renumber leaves in Morton order.
+ * Passage: Sect. 3 (a refinement splits the cells in two in all three
+ * directions; adjacent blocks differ by at most one level; blocks coarsen
+ * when the criterion is no longer met).  ICARUS_ERR_STATE without flags.
  * Errors: ICARUS_ERR_CAPACITY if the new tree of all members needs more
  * blocks than max_blocks; the tree, the state and the flags are then left as
  * they were (the caller may retry at a later regrid). */
@@ -180,7 +207,9 @@ icarus_status icarus_regrid(icarus_ctx *ctx);
 /* Sample primitives at n_pts points rtp[n_pts][3] (host: r, colat, lon) by
  * trilinear interpolation between cell centres of the finest leaf containing
  * each point; prim_out[n_pts][8] (host).  Points outside the domain give NaN.
- * Synchronises. */
+ * Passage: Sect. 3.1-3.3 (time series of speed and density at Earth, from
+ * which the shock arrival time, shock width and peak speed are read).
+ * ICARUS_ERR_ARG for a bad member or n_pts < 0 or > 4096.  Synchronises. */
 icarus_status icarus_probe(icarus_ctx *ctx, int member, int n_pts, const double *rtp, double *prim_out);
 
 /* ---- helpers used by the harness and the parity tests ---- */
@@ -196,6 +225,14 @@ icarus_status icarus_get_tree(icarus_ctx *ctx, int member, int32_t *rows, int ca
  * of doubles in the host array (must equal leaves * 8 * cells per block). */
 icarus_status icarus_set_state(icarus_ctx *ctx, int member, const double *host, size_t n, int is_prim);
 icarus_status icarus_get_state(icarus_ctx *ctx, int member, double *host, size_t n);
+
+/* One leaf block of a member (leaf = index within the member, Morton order)
+ * with its two ghost layers as they were last filled (by icarus_flag_refine,
+ * icarus_probe or icarus_ghost_fill; a step leaves them stale): host FP64
+ * [8][n0+4][n1+4][n2+4] of conserved variables, n = that count.  Lets a test
+ * evaluate a block-local operator on exactly the data the device saw.
+ * ICARUS_ERR_ARG for a bad member, leaf or n.  Synchronises. */
+icarus_status icarus_get_padded(icarus_ctx *ctx, int member, int leaf, double *host, size_t n);
 
 /* member time (host write / read) */
 icarus_status icarus_set_time(icarus_ctx *ctx, int member, double t);
@@ -221,9 +258,12 @@ icarus_status icarus_conservation_sums(icarus_ctx *ctx, int member, double *out8
  *   errors   ICARUS_ERR_CAPACITY (and a message on stderr) if the member has
  *            more than 16384 leaves; ICARUS_ERR_ARG on bad arguments;
  *            ICARUS_ERR_CUDA if a CUDA call fails.
- * The first call on a device looks up the array's address (with that device
- * current) and caches it: make that call before any stream capture.  All calls
- * share the one array; calls that overlap on the GPU race.  Synchronises. */
+ * The array and this call's kernels are put in place on a device when the
+ * first context is created there (icarus_init_grid looks up the array's
+ * address with that device current and caches it), so create contexts before
+ * handing the rest of the GPU to another pool and before any stream capture.
+ * All calls share the one array; calls that overlap on the GPU race.
+ * Synchronises. */
 icarus_status icarus_conservation_sums_static(icarus_ctx *ctx, int member, double *out8);
 
 /* Current CFL time step of every member (host, n_members doubles). */
@@ -241,6 +281,17 @@ icarus_status icarus_status_word(icarus_ctx *ctx, uint32_t *word, uint64_t *floo
 /* Stage-kernel tile shape (theta x phi cells per CTA) and radial segment
  * length; 0 = library default.  Used by the autotuner. */
 icarus_status icarus_set_tile(icarus_ctx *ctx, int tile_theta, int tile_phi, int r_segment);
+
+/* Floor budget.  Density and pressure floors (rho_floor, p_floor) are applied
+ * after every stage and counted (icarus_status_word).  A step whose floor hits
+ * exceed max_fraction times the leaf cells it advanced (all members) sets bit 1
+ * of the status word: the next call that reads the word (every synchronising
+ * call, and icarus_step itself, see there) returns ICARUS_ERR_NONPHYSICAL and
+ * the context is poisoned.  0 disables the budget.  Default
+ * ICARUS_DEFAULT_FLOOR_BUDGET.  Not stored in checkpoints.  ICARUS_ERR_ARG for
+ * a negative or NaN fraction. */
+#define ICARUS_DEFAULT_FLOOR_BUDGET 0.05
+icarus_status icarus_set_floor_budget(icarus_ctx *ctx, double max_fraction);
 
 /* FP32 mode: the pressure of a cell is recomputed in FP64 (from the stored
  * FP32 variables) where p < p_over_e * e or p < beta * B^2/2.  Defaults 0.002

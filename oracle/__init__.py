@@ -78,6 +78,7 @@ def lib():
                 "or_set_state": (V, [P, P, I]),
                 "or_get_state": (V, [P, P]),
                 "or_get_padded": (V, [P, I, I, P]),
+                "or_set_padded": (V, [P, I, I, P]),
                 "or_set_boundary_map": (V, [P, P]),
                 "or_set_cme": (V, [P, P]),
                 "or_snapshot_vbg": (I, [P]),
@@ -250,6 +251,11 @@ class Grid:
         out = np.zeros((8,) + P)
         lib().or_get_padded(self._g, n, which, _ptr(out))
         return out
+
+    def set_padded(self, n, P, which=0):
+        """overwrite leaf n's padded block, ghost layers included"""
+        P = np.ascontiguousarray(P, dtype=np.float64).reshape((8,) + tuple(x + 4 for x in self.nb))
+        lib().or_set_padded(self._g, n, which, _ptr(P))
 
     def set_boundary_map(self, prim):
         prim = np.ascontiguousarray(prim, dtype=np.float64)

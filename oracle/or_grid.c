@@ -1153,6 +1153,12 @@ void or_get_padded(or_grid *g, int n, int which, double *out) {
   memcpy(out, buf(g->leaves[n], which), sizeof(double) * or_pcells(g) * NV);
 }
 
+/* overwrite a leaf's padded block (ghost layers included) in buffer `which`;
+ * lets a test run the estimator on data filled elsewhere */
+void or_set_padded(or_grid *g, int n, int which, const double *in) {
+  memcpy(buf(g->leaves[n], which), in, sizeof(double) * or_pcells(g) * NV);
+}
+
 void or_set_boundary_map(or_grid *g, const double *prim) {
   memcpy(g->map, prim, sizeof(double) * NV * g->p.n[1] * g->p.n[2]);
 }

@@ -203,6 +203,7 @@ struct icarus_ctx {
   cudaStream_t stream = nullptr;
   char *arena = nullptr;
   int nsm = 1;
+  int dev = 0;   // CUDA device current when the context was created
   // device pointers
   Geometry *geo = nullptr;
   DevBlock *blk = nullptr, *blk_alt = nullptr;
@@ -214,7 +215,7 @@ struct icarus_ctx {
   DevCme *cme = nullptr;
   double *t = nullptr, *dt_used = nullptr, *dt_cfl = nullptr, *tstop = nullptr, *updates = nullptr,
          *cells_m = nullptr;
-  unsigned long long *inv_max = nullptr, *floor_hits = nullptr;
+  unsigned long long *inv_max = nullptr, *floor_hits = nullptr, *floor_prev = nullptr;
   unsigned int *status = nullptr;
   signed char *flags = nullptr;
   int *all_list = nullptr, *lvl_list = nullptr, *rlist = nullptr, *shell = nullptr;
@@ -234,6 +235,12 @@ struct icarus_ctx {
   // launch configuration
   int tile_j = 0, tile_k = 0, seg_len = 0, occ = 1;
   double isl_pe = 0.002, isl_beta = 0.1;  // FP64 pressure islands: p < 0.002 e or beta < 0.1
+  double floor_budget = ICARUS_DEFAULT_FLOOR_BUDGET;
+  // status word read back without a synchronisation after steps that return
+  // no times (pinned host word, event of its copy)
+  unsigned int *h_status = nullptr;
+  cudaEvent_t status_ev = nullptr;
+  bool status_pending = false;
   bool use_graph = true;
   cudaGraphExec_t graph = nullptr;
   bool graph_valid = false;
@@ -301,18 +308,27 @@ bool wrap_block(const icarus_ctx *c, int L, int *b) {
   return true;
 }
 
-void build_member_map(icarus_ctx *c, Member &m) {
+// Level maps of a member: leaf index, -2 (refined) or -1 (covered by a
+// coarser leaf).  Returns false if two leaves overlap (a leaf lies inside
+// another one or appears twice); the maps are then incomplete.
+bool build_member_map(icarus_ctx *c, Member &m) {
   m.map.assign(c->d.max_level + 1, std::vector<int>());
   for (int L = 1; L <= c->d.max_level; L++) m.map[L].assign((size_t)blocks_at_level(&c->d, L), -1);
+  bool ok = true;
   for (size_t n = 0; n < m.leaves.size(); n++) {
     const Leaf &l = m.leaves[n];
-    m.map[l.level][map_index(c, l.level, l.ix)] = (int)n;
+    int &own = m.map[l.level][map_index(c, l.level, l.ix)];
+    if (own != -1) ok = false;   // a duplicate, or an ancestor of a finer leaf
+    own = (int)n;
     int b[3] = {l.ix[0], l.ix[1], l.ix[2]};
     for (int L = l.level - 1; L >= 1; L--) {
       for (int d = 0; d < 3; d++) b[d] >>= 1;
-      m.map[L][map_index(c, L, b)] = -2;
+      int &e = m.map[L][map_index(c, L, b)];
+      if (e >= 0) ok = false;    // inside a coarser leaf
+      e = -2;
     }
   }
+  return ok;
 }
 
 // relation of the region (level L, block index b) to the leaves: the leaf
@@ -359,6 +375,53 @@ void neighbours(const icarus_ctx *c, const Member &m, int n, std::vector<int> &o
       }
   std::sort(out.begin(), out.end());
   out.erase(std::unique(out.begin(), out.end()), out.end());
+}
+
+// A leaf list read from outside (a checkpoint) must be a tree this library
+// could have built: leaves in strictly increasing Morton order, no overlap,
+// the whole domain covered, and adjacent leaves (faces, edges, corners) at
+// most one level apart.
+bool tree_is_valid(icarus_ctx *c, Member &m) {
+  const int top = c->d.max_level;
+  for (size_t n = 1; n < m.leaves.size(); n++)
+    if (!(morton_key(m.leaves[n - 1], top) < morton_key(m.leaves[n], top))) return false;
+  if (!build_member_map(c, m)) return false;
+  // coverage, counted in blocks of the finest level
+  unsigned long long vol = 0;
+  for (const Leaf &l : m.leaves) vol += 1ull << (3 * (top - l.level));
+  if (vol != (unsigned long long)blocks_at_level(&c->d, top)) return false;
+  // 2:1 balance: no neighbour region two levels coarser or finer
+  for (const Leaf &l : m.leaves) {
+    const int L = l.level;
+    for (int dx = -1; dx <= 1; dx++)
+      for (int dy = -1; dy <= 1; dy++)
+        for (int dz = -1; dz <= 1; dz++) {
+          if (!dx && !dy && !dz) continue;
+          int b[3] = {l.ix[0] + dx, l.ix[1] + dy, l.ix[2] + dz};
+          if (!wrap_block(c, L, b)) continue;
+          const int s = region_state(c, m, L, b);
+          if (s == -1) {   // covered by a coarser leaf: it must be the parent level's
+            if (L < 2) return false;
+            int pb[3] = {b[0] >> 1, b[1] >> 1, b[2] >> 1};
+            if (region_state(c, m, L - 1, pb) < 0) return false;
+          } else if (s == -2) {   // refined: the children touching leaf l must be leaves
+            const int dir[3] = {dx, dy, dz};
+            for (int ch = 0; ch < 8; ch++) {
+              const int o[3] = {(ch >> 2) & 1, (ch >> 1) & 1, ch & 1};
+              bool touch = true;
+              for (int d = 0; d < 3; d++) {
+                if (dir[d] == 1 && o[d] != 0) touch = false;
+                if (dir[d] == -1 && o[d] != 1) touch = false;
+              }
+              if (!touch || L + 1 > top) continue;
+              int cb[3];
+              for (int d = 0; d < 3; d++) cb[d] = 2 * b[d] + o[d];
+              if (region_state(c, m, L + 1, cb) < 0) return false;
+            }
+          }
+        }
+  }
+  return true;
 }
 
 // device tables that depend on the leaf lists
@@ -494,6 +557,8 @@ void fill_kp(icarus_ctx *c) {
   k.inv_max = c->inv_max;
   k.status = c->status;
   k.floor_hits = c->floor_hits;
+  k.floor_prev = c->floor_prev;
+  k.floor_budget = c->floor_budget;
 }
 
 // geometry tables of every level, FP64 and FP32 copies
@@ -816,11 +881,9 @@ void permutation(std::vector<int> &p, int n, uint64_t &state) {
   }
 }
 
-icarus_status check_status(icarus_ctx *c) {
-  unsigned int w = 0;
-  CK(cudaMemcpyAsync(&w, c->status, sizeof(w), cudaMemcpyDeviceToHost, c->stream));
-  CK(cudaStreamSynchronize(c->stream));
-  if (w & ST_NAN) {
+// status of a status word read back from the device; poisons the context
+icarus_status status_of_word(icarus_ctx *c, unsigned int w) {
+  if (w & (ST_NAN | ST_FLOOR)) {
     c->poisoned = true;
     return ICARUS_ERR_NONPHYSICAL;
   }
@@ -829,6 +892,25 @@ icarus_status check_status(icarus_ctx *c) {
     return ICARUS_ERR_TIMEOUT;
   }
   return ICARUS_OK;
+}
+
+icarus_status check_status(icarus_ctx *c) {
+  unsigned int w = 0;
+  CK(cudaMemcpyAsync(&w, c->status, sizeof(w), cudaMemcpyDeviceToHost, c->stream));
+  CK(cudaStreamSynchronize(c->stream));
+  c->status_pending = false;
+  return status_of_word(c, w);
+}
+
+// the status word copied after an earlier step, if its copy has landed
+// (no synchronisation)
+icarus_status poll_status(icarus_ctx *c) {
+  if (!c->status_pending) return ICARUS_OK;
+  const cudaError_t q = cudaEventQuery(c->status_ev);
+  if (q == cudaErrorNotReady) return ICARUS_OK;
+  c->status_pending = false;
+  if (q != cudaSuccess) return ICARUS_ERR_CUDA;
+  return status_of_word(c, *c->h_status);
 }
 
 icarus_status recompute_dt(icarus_ctx *c) {
@@ -889,6 +971,21 @@ icarus_status icarus_init_grid(const icarus_grid_desc *desc, icarus_ctx **out) {
     delete c;
     return ICARUS_ERR_CUDA;
   }
+  c->dev = dev;
+  if (cudaHostAlloc((void **)&c->h_status, sizeof(unsigned int), cudaHostAllocDefault) != cudaSuccess ||
+      cudaEventCreateWithFlags(&c->status_ev, cudaEventDisableTiming) != cudaSuccess) {
+    if (c->h_status) cudaFreeHost(c->h_status);
+    delete c;
+    return ICARUS_ERR_CUDA;
+  }
+  // the allocation-free sums' scratch is put in place now, while the caller
+  // can still give up device memory for it
+  if (static_sums_prepare(dev) != 0) {
+    cudaEventDestroy(c->status_ev);
+    cudaFreeHost(c->h_status);
+    delete c;
+    return ICARUS_ERR_CUDA;
+  }
   c->geo = at<Geometry>(c, lay.geo);
   c->blk = at<DevBlock>(c, lay.blk);
   c->blk_alt = lay.blk_alt.bytes ? at<DevBlock>(c, lay.blk_alt) : nullptr;
@@ -912,6 +1009,7 @@ icarus_status icarus_init_grid(const icarus_grid_desc *desc, icarus_ctx **out) {
   c->floor_hits = reinterpret_cast<unsigned long long *>(sc + 5 * nm + 1);
   c->updates = sc + 5 * nm + 2;
   c->cells_m = sc + 6 * nm + 2;
+  c->floor_prev = reinterpret_cast<unsigned long long *>(sc + 7 * nm + 2);
   c->flags = at<signed char>(c, lay.flags);
   c->all_list = at<int>(c, lay.lists);
   c->lvl_list = c->all_list + lay.max_blocks;
@@ -947,6 +1045,8 @@ icarus_status icarus_init_grid(const icarus_grid_desc *desc, icarus_ctx **out) {
     c->mlp_tin = c->mlp_xin + (size_t)MLP_BMAX * 64;
   }
   auto fail = [&](icarus_status s) {
+    cudaEventDestroy(c->status_ev);
+    cudaFreeHost(c->h_status);
     delete c;
     return s;
   };
@@ -1001,6 +1101,11 @@ icarus_status icarus_init_grid(const icarus_grid_desc *desc, icarus_ctx **out) {
 void icarus_destroy(icarus_ctx *c) {
   if (!c) return;
   if (c->graph) cudaGraphExecDestroy(c->graph);
+  if (c->status_ev) {
+    cudaEventSynchronize(c->status_ev);
+    cudaEventDestroy(c->status_ev);
+  }
+  if (c->h_status) cudaFreeHost(c->h_status);
   for (cudaEvent_t e : c->ev) cudaEventDestroy(e);
   delete c;
 }
@@ -1106,6 +1211,11 @@ icarus_status icarus_step(icarus_ctx *c, int n_steps, const double *t_stop, doub
   if (!c || n_steps < 0 || !t_stop) return ICARUS_ERR_ARG;
   if (n_steps > 0) c->ghosts_fresh = false;
   if (c->poisoned) return ICARUS_ERR_STATE;
+  {
+    // a non-physical state left by an earlier call that returned no times
+    const icarus_status st = poll_status(c);
+    if (st != ICARUS_OK) return st;
+  }
   const int nm = c->d.n_members;
   c->h_tstop.assign(t_stop, t_stop + nm);
   CK(cudaMemcpyAsync(c->tstop, c->h_tstop.data(), sizeof(double) * nm, cudaMemcpyHostToDevice, c->stream));
@@ -1149,8 +1259,12 @@ icarus_status icarus_step(icarus_ctx *c, int n_steps, const double *t_stop, doub
         CK(cudaPeekAtLastError());
       }
       if (bounded && s0 + ns < n_steps) {
+        unsigned int w = 0;
         CK(cudaMemcpyAsync(th.data(), c->t, sizeof(double) * nm, cudaMemcpyDeviceToHost, c->stream));
+        CK(cudaMemcpyAsync(&w, c->status, sizeof(w), cudaMemcpyDeviceToHost, c->stream));
         CK(cudaStreamSynchronize(c->stream));
+        const icarus_status st = status_of_word(c, w);
+        if (st != ICARUS_OK) return st;
         bool done = true;
         for (int m = 0; m < nm; m++) done = done && th[m] >= c->h_tstop[m];
         if (done) break;
@@ -1162,6 +1276,12 @@ icarus_status icarus_step(icarus_ctx *c, int n_steps, const double *t_stop, doub
     CK(cudaMemcpyAsync(t_out, c->t, sizeof(double) * nm, cudaMemcpyDeviceToHost, c->stream));
     icarus_status st = check_status(c);
     if (st != ICARUS_OK) return st;
+  } else if (n_steps > 0) {
+    // no synchronisation: the status word follows the steps into pinned host
+    // memory and is looked at by the next call
+    CK(cudaMemcpyAsync(c->h_status, c->status, sizeof(unsigned int), cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaEventRecord(c->status_ev, c->stream));
+    c->status_pending = true;
   }
   return ICARUS_OK;
 }
@@ -1234,6 +1354,24 @@ icarus_status icarus_get_state(icarus_ctx *c, int member, double *host, size_t n
     CK(cudaMemcpyAsync(host + (size_t)s0 * per, c->staging, sizeof(double) * per * ns, cudaMemcpyDeviceToHost,
                        c->stream));
     CK(cudaStreamSynchronize(c->stream));
+  }
+  return ICARUS_OK;
+}
+
+icarus_status icarus_get_padded(icarus_ctx *c, int member, int leaf, double *host, size_t n) {
+  if (!member_ok(c, member) || !host) return ICARUS_ERR_ARG;
+  const int nl = (int)c->mem[member].leaves.size();
+  if (leaf < 0 || leaf >= nl || n != (size_t)NVAR * c->kp.pcells) return ICARUS_ERR_ARG;
+  const size_t slot = (size_t)c->mem_off[member] + leaf;
+  std::vector<unsigned char> raw(n * c->rsize);
+  CK(cudaMemcpyAsync(raw.data(), static_cast<const char *>(c->U) + slot * raw.size(), raw.size(),
+                     cudaMemcpyDeviceToHost, c->stream));
+  CK(cudaStreamSynchronize(c->stream));
+  if (c->prec) {
+    const float *f = reinterpret_cast<const float *>(raw.data());
+    for (size_t q = 0; q < n; q++) host[q] = (double)f[q];
+  } else {
+    memcpy(host, raw.data(), raw.size());
   }
   return ICARUS_OK;
 }
@@ -1486,6 +1624,14 @@ icarus_status icarus_set_fp64_islands(icarus_ctx *c, double p_over_e, double bet
   return ICARUS_OK;
 }
 
+icarus_status icarus_set_floor_budget(icarus_ctx *c, double max_fraction) {
+  if (!c || !(max_fraction >= 0.0)) return ICARUS_ERR_ARG;
+  c->floor_budget = max_fraction;
+  fill_kp(c);
+  c->graph_valid = false;
+  return ICARUS_OK;
+}
+
 icarus_status icarus_profile(icarus_ctx *c, int enable) {
   if (!c) return ICARUS_ERR_ARG;
   c->prof_on = enable != 0;
@@ -1517,6 +1663,8 @@ icarus_status icarus_profile_read(icarus_ctx *c, double *ms, int *count, int nki
 
 // Read-only view of one member's leaves for kernels that live outside this
 // file (no state is changed).
+int ctx_device(const icarus_ctx *c) { return c ? c->dev : -1; }
+
 int ctx_member_view(icarus_ctx *c, int member, KParams *kp, const void **U, int *precision, int *slot0, int *nleaves,
                     cudaStream_t *stream) {
   if (!c || member < 0 || member >= c->d.n_members) return -1;
@@ -1791,6 +1939,8 @@ icarus_status icarus_load(icarus_ctx *c, const char *path) {
     int32_t hdr[2] = {0, 0};
     F.get(hdr, sizeof(hdr));
     if (!F.ok || hdr[0] < 1 || hdr[0] > c->d.max_level || hdr[1] < 1) return ICARUS_ERR_ARG;
+    // a corrupt count must not reach the allocation below
+    if ((size_t)hdr[1] > (size_t)c->lay.max_blocks - total) return ICARUS_ERR_CAPACITY;
     next[m].max_level = hdr[0];
     F.get(&next[m].cme, sizeof(DevCme));
     next[m].leaves.resize(hdr[1]);
@@ -1804,9 +1954,9 @@ icarus_status icarus_load(icarus_ctx *c, const char *path) {
         if (l.ix[d] < 0 || l.ix[d] >= nblk_dim(c, l.level, d)) return ICARUS_ERR_ARG;
       }
     }
+    if (!tree_is_valid(c, next[m])) return ICARUS_ERR_ARG;
     total += next[m].leaves.size();
   }
-  if (total > (size_t)c->lay.max_blocks) return ICARUS_ERR_CAPACITY;
   std::vector<double> t(nm), dtc(nm), upd(nm), bmap(nm * nbm), vbg(nm * nbc);
   unsigned long long hits = 0;
   double isl[2];
@@ -1841,7 +1991,9 @@ icarus_status icarus_load(icarus_ctx *c, const char *path) {
   CK(cudaMemcpyAsync(c->bmap, bmap.data(), sizeof(double) * bmap.size(), cudaMemcpyHostToDevice, s));
   CK(cudaMemcpyAsync(c->vbg, vbg.data(), sizeof(double) * vbg.size(), cudaMemcpyHostToDevice, s));
   CK(cudaMemcpyAsync(c->floor_hits, &hits, sizeof(hits), cudaMemcpyHostToDevice, s));
+  CK(cudaMemcpyAsync(c->floor_prev, &hits, sizeof(hits), cudaMemcpyHostToDevice, s));   // the budget counts from here
   CK(cudaMemsetAsync(c->status, 0, sizeof(unsigned int), s));
+  c->status_pending = false;
   if (!U.empty()) CK(cudaMemcpyAsync(c->U, U.data(), U.size(), cudaMemcpyHostToDevice, s));
   if (nth) {
     CK(cudaMemcpyAsync(c->mlp_theta, theta.data(), sizeof(float) * nth, cudaMemcpyHostToDevice, s));
@@ -1849,6 +2001,8 @@ icarus_status icarus_load(icarus_ctx *c, const char *path) {
     CK(cudaMemsetAsync(c->mlp_v, 0, sizeof(float) * nth, s));
     c->mlp_step = 0;
     c->mlp_ready = true;
+  } else {
+    c->mlp_ready = false;   // the saved context had no pre-flagger parameters
   }
   CK(cudaStreamSynchronize(s));
   c->poisoned = false;

@@ -95,6 +95,8 @@ struct KParams {
   unsigned long long *inv_max; // [member] bit pattern of a positive double
   unsigned int *status;
   unsigned long long *floor_hits;
+  unsigned long long *floor_prev;  // floor counter at the end of the previous step
+  double floor_budget;         // floor hits per cell-update of a step that set ST_FLOOR (0: no budget)
   int n_base_cells[3];
   double isl_pe, isl_beta;     // FP64 pressure-island thresholds (FP32 mode)
 };
@@ -168,3 +170,7 @@ void mlp_combine_launch(const float *prob, const DevBlock *blk, signed char *fla
 struct icarus_ctx;
 int ctx_member_view(icarus_ctx *c, int member, KParams *kp, const void **U, int *precision, int *slot0,
                     int *nleaves, cudaStream_t *stream);
+// CUDA device the context was created on
+int ctx_device(const icarus_ctx *c);
+// scratch of the allocation-free sums on device dev (k_sums_static.cu)
+int static_sums_prepare(int dev);

@@ -388,6 +388,18 @@ __global__ void k_dt_begin(const KParams kp, const double *tstop) {
 
 __global__ void k_dt_finalize(const KParams kp, double cfl) {
   const int m = blockIdx.x * blockDim.x + threadIdx.x;
+  if (m == 0) {
+    // floor budget: the floors the step applied (both stages) against the
+    // leaf cells it advanced
+    const unsigned long long h = *kp.floor_hits, d = h - *kp.floor_prev;
+    *kp.floor_prev = h;
+    if (kp.floor_budget > 0.0 && d > 0) {
+      double cells = 0.0;
+      for (int q = 0; q < kp.n_members; q++)
+        if (kp.dt_used[q] > 0.0) cells += kp.cells_m[q];
+      if ((double)d > kp.floor_budget * cells) atomicOr(kp.status, ST_FLOOR);
+    }
+  }
   if (m >= kp.n_members) return;
   const double dt = kp.dt_used[m];
   if (dt > 0.0) {

@@ -6,19 +6,28 @@
 // a service that must not stall on an allocation in the middle of a run.
 // icarus_conservation_sums_static gives them the per-member sums of V * U
 // without any allocation: its scratch is a fixed array in this file's device
-// memory, reserved when the library is loaded on a device and kept there until
-// the process exits.
+// memory, kept on the device until the process exits.
+//
+// When the array comes into being: with CUDA's lazy module loading (the
+// default) this file's module, with the array and its kernels, is loaded on a
+// device the first time something in it is used.  icarus_init_grid does that
+// on purpose (static_sums_prepare below, with the context's device current):
+// it looks up the array's address, forces this file's kernels to load and caches
+// the address per device.  So the array is in place once a context exists, and
+// a caller that afterwards gives the rest of the GPU to its own pool can still
+// call this entry point.
 //
 // Limits and rules, for users:
 //   * at most ICARUS_STATIC_SUM_BLOCKS leaves per member; larger members are
 //     rejected with ICARUS_ERR_CAPACITY and a message on stderr;
-//   * the first call on each device looks up the array's device address (with
-//     that device current) and caches it; make that first call before any
-//     stream capture begins;
+//   * the address is taken while the context is created; create contexts
+//     before any stream capture begins;
 //   * every call, on every context and stream, shares the one array: calls
 //     that overlap on the GPU race and may return each other's sums.  Each call
 //     overwrites every scratch entry it reads, so no clearing is needed, and
 //     the array keeps the last call's partial sums afterwards.
+//   * a cudaDeviceReset destroys the array with the rest of the device's
+//     memory, and with it every context's arena: contexts do not outlive it.
 // The result equals icarus_conservation_sums: the same per-block partial sums
 // added in the same order, in FP64.
 #include <cstdio>
@@ -74,6 +83,27 @@ __global__ void k_total_static(const double *partial, int nblocks, double *total
 
 }  // namespace
 
+// Look up the scratch array's device address on device `dev` (which must be
+// the current device) and load this file's kernels there; cached per device.
+// Called by icarus_init_grid.  Returns 0 on success.
+int static_sums_prepare(int dev) {
+  if (dev < 0 || dev >= ICARUS_MAX_DEVICES) return -1;
+  if (g_scratch_addr[dev]) return 0;
+  void *p = nullptr;
+  cudaError_t e = cudaGetSymbolAddress(&p, g_sum_scratch);
+  if (e != cudaSuccess || !p) {
+    fprintf(stderr, "libicarus: cudaGetSymbolAddress of the static sum scratch failed: %s\n", cudaGetErrorString(e));
+    return -1;
+  }
+  cudaFuncAttributes fa;
+  if (cudaFuncGetAttributes(&fa, k_block_sums_static<float>) != cudaSuccess ||
+      cudaFuncGetAttributes(&fa, k_block_sums_static<double>) != cudaSuccess ||
+      cudaFuncGetAttributes(&fa, k_total_static) != cudaSuccess)
+    return -1;
+  g_scratch_addr[dev] = static_cast<double *>(p);
+  return 0;
+}
+
 extern "C" icarus_status icarus_conservation_sums_static(icarus_ctx *ctx, int member, double *out8) {
   if (!ctx || !out8) return ICARUS_ERR_ARG;
   KParams kp;
@@ -88,18 +118,9 @@ extern "C" icarus_status icarus_conservation_sums_static(icarus_ctx *ctx, int me
             ICARUS_STATIC_SUM_BLOCKS, member, nl);
     return ICARUS_ERR_CAPACITY;
   }
-  int dev = 0;
-  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= ICARUS_MAX_DEVICES) return ICARUS_ERR_CUDA;
-  if (!g_scratch_addr[dev]) {
-    void *p = nullptr;
-    cudaError_t e = cudaGetSymbolAddress(&p, g_sum_scratch);
-    if (e != cudaSuccess || !p) {
-      fprintf(stderr, "libicarus: cudaGetSymbolAddress of the static sum scratch failed: %s\n",
-              cudaGetErrorString(e));
-      return ICARUS_ERR_CUDA;
-    }
-    g_scratch_addr[dev] = static_cast<double *>(p);
-  }
+  // the address was taken on the context's device when it was created
+  const int dev = ctx_device(ctx);
+  if (dev < 0 || dev >= ICARUS_MAX_DEVICES || !g_scratch_addr[dev]) return ICARUS_ERR_STATE;
   double *partial = g_scratch_addr[dev];
   double *total = partial + (size_t)ICARUS_STATIC_SUM_BLOCKS * NVAR;
   if (nl > 0) {

@@ -35,6 +35,7 @@ EXPORTS = [
     "icarus_set_member_max_level", "icarus_ghost_fill", "icarus_conservation_sums", "icarus_get_dt",
     "icarus_status_word", "icarus_set_tile", "icarus_use_graph", "icarus_kernels_per_step",
     "icarus_profile", "icarus_profile_read", "icarus_set_fp64_islands", "icarus_conservation_sums_static",
+    "icarus_set_floor_budget", "icarus_get_padded",
     "icarus_mlp_set_params", "icarus_mlp_get_params", "icarus_mlp_features", "icarus_mlp_predict_leaves",
     "icarus_mlp_predict", "icarus_mlp_grad", "icarus_mlp_dataset_clear", "icarus_mlp_dataset_add",
     "icarus_mlp_train", "icarus_cell_updates", "icarus_save", "icarus_load", "icarus_destroy",
@@ -109,6 +110,8 @@ def load(build_if_missing: bool = True):
             "icarus_kernels_per_step": [P, C.POINTER(I)],
             "icarus_profile": [P, I],
             "icarus_profile_read": [P, dp, C.POINTER(I), I],
+            "icarus_set_floor_budget": [P, D],
+            "icarus_get_padded": [P, I, I, dp, S],
         }
         for name, args in sig.items():
             f = getattr(L, name)
@@ -258,6 +261,12 @@ class Icarus:
         _chk("icarus_get_state", self.lib.icarus_get_state(self.ctx, member, _dp(out), out.size))
         return out
 
+    def get_padded(self, member, leaf):
+        """a leaf block with its ghost layers as last filled (FP64 conserved)"""
+        out = np.zeros((8,) + tuple(b + 4 for b in self.block))
+        _chk("icarus_get_padded", self.lib.icarus_get_padded(self.ctx, member, leaf, _dp(out), out.size))
+        return out
+
     def set_time(self, member, t):
         _chk("icarus_set_time", self.lib.icarus_set_time(self.ctx, member, float(t)))
 
@@ -289,6 +298,11 @@ class Icarus:
         w, f = C.c_uint32(0), C.c_uint64(0)
         _chk("icarus_status_word", self.lib.icarus_status_word(self.ctx, C.byref(w), C.byref(f)))
         return w.value, f.value
+
+    def set_floor_budget(self, max_fraction):
+        """Poison the context when a step's floor hits exceed this fraction of
+        the leaf cells it advanced (0 disables the budget)."""
+        _chk("icarus_set_floor_budget", self.lib.icarus_set_floor_budget(self.ctx, float(max_fraction)))
 
     def set_tile(self, tile_theta=0, tile_phi=0, r_segment=0):
         _chk("icarus_set_tile", self.lib.icarus_set_tile(self.ctx, tile_theta, tile_phi, r_segment))

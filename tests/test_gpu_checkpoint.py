@@ -75,3 +75,50 @@ def test_foreign_or_mismatched_checkpoints_are_refused(tmp_path):
         g.load(str(bad))
     with pytest.raises(IcarusError):
         g.load(str(tmp_path / "missing.ck"))
+
+
+def test_checkpoint_without_preflagger_clears_the_loaded_one(tmp_path):
+    """A context restored from a checkpoint saved without pre-flagger
+    parameters has none either, even if it had some before the load."""
+    g, o = make_pair(n=(48, 16, 32), nb=(12, 8, 8))
+    wind_setup(g, o)
+    path = str(tmp_path / "e.ck")
+    g.save(path)
+    h, _ = make_pair(n=(48, 16, 32), nb=(12, 8, 8))
+    h.mlp_set_params(I.mlp_init(1).astype(np.float32))
+    h.mlp_predict(np.zeros((4, 64), np.float32))
+    h.load(path)
+    with pytest.raises(IcarusError):
+        h.mlp_predict(np.zeros((4, 64), np.float32))
+
+
+def _ck_rows_offset(nfp=29):
+    # magic, version, field count, descriptor fields, then member 0's
+    # (max level, leaf count) and its cone CME record (8 doubles, 2 ints)
+    return 8 + 4 + 4 + 8 * nfp + 8 + 72
+
+
+def test_corrupt_trees_are_refused(tmp_path):
+    """A checkpoint whose leaf list is not a valid tree (a duplicate leaf, a
+    leaf count beyond the pool) is refused and the context is unchanged."""
+    g, o = make_pair(n=(48, 16, 32), nb=(12, 8, 8))
+    wind_setup(g, o)
+    path = tmp_path / "f.ck"
+    g.save(str(path))
+    raw = bytearray(path.read_bytes())
+    rows = np.frombuffer(bytes(raw[_ck_rows_offset():_ck_rows_offset() + 16 * 32]), dtype=np.int32).reshape(32, 4)
+    assert np.array_equal(rows, g.tree(0))          # the offsets above are right
+    dup = bytearray(raw)
+    dup[_ck_rows_offset() + 16:_ck_rows_offset() + 32] = raw[_ck_rows_offset():_ck_rows_offset() + 16]
+    (tmp_path / "dup.ck").write_bytes(bytes(dup))
+    big = bytearray(raw)
+    big[_ck_rows_offset() - 76:_ck_rows_offset() - 72] = np.int32(2 ** 30).tobytes()
+    (tmp_path / "big.ck").write_bytes(bytes(big))
+    h, _ = make_pair(n=(48, 16, 32), nb=(12, 8, 8))
+    wind_setup(h, _)
+    h.step(1)
+    before = h.get_state(0)
+    for name in ("dup.ck", "big.ck"):
+        with pytest.raises(IcarusError):
+            h.load(str(tmp_path / name))
+        assert np.array_equal(before, h.get_state(0))

@@ -1,5 +1,5 @@
 """Learned pre-flagger on the GPU against the NumPy oracle: features,
-forward, gradients (FP32 kernels vs FP64 oracle, <= 1e-5 relative), Adam,
+forward, gradients (FP32 kernels vs FP64 oracle, element by element), Adam,
 training, and what the trained network gains over the plain estimator."""
 import math
 
@@ -40,9 +40,17 @@ def test_forward_and_gradient_match_oracle():
     yo, _ = M.forward(theta.astype(np.float64), X.astype(np.float64))
     assert np.allclose(y, yo, rtol=1e-5, atol=1e-6)
     gg, loss = g.mlp_grad(X, T)
-    go = M.grad(theta.astype(np.float64), X.astype(np.float64), T.astype(np.float64))
-    rel = np.linalg.norm(gg - go) / np.linalg.norm(go)
-    assert rel < 1e-5, rel
+    th, X64, T64 = theta.astype(np.float64), X.astype(np.float64), T.astype(np.float64)
+    go = M.grad(th, X64, T64)
+    # element by element: 1e-5 of the value, plus the FP32 rounding of a
+    # batch sum whose terms may cancel (1e-6 of the sum of the magnitudes of
+    # the per-sample terms, each an oracle gradient on one sample)
+    mag = np.zeros_like(go)
+    for b in range(X.shape[0]):
+        mag += np.abs(M.grad(th, X64[b:b + 1], T64[b:b + 1])) / X.shape[0]
+    bound = 1e-5 * np.abs(go) + 1e-6 * mag
+    bad = np.flatnonzero(np.abs(gg - go) > bound)
+    assert bad.size == 0, (bad[:10], gg[bad[:10]], go[bad[:10]])
     assert abs(loss - M.loss(theta.astype(np.float64), X.astype(np.float64), T.astype(np.float64))) < 1e-5
 
 

@@ -49,9 +49,11 @@ def _sod(N, gamma, t_end=0.2):
 def test_sod_shock_tube_converges_to_exact(gamma):
     e = [_sod(N, gamma)[0] for N in (100, 200, 400)]
     assert e[0] > e[1] > e[2]
-    order = math.log2(e[1] / e[2])
-    # discontinuous solution: first order or a little below it for a TVD scheme
-    assert order >= 0.6, e
+    # discontinuous solution: a TVD scheme converges at first order or a
+    # little below it in L1 (the contact is smeared over a growing number of
+    # cells); measured 0.90 (gamma 1.4) and 1.02 (gamma 1.5) over 200 -> 400
+    assert math.log2(e[1] / e[2]) >= 0.8, e
+    assert 0.5 * math.log2(e[0] / e[2]) >= 0.8, e
     assert e[2] < 0.01
 
 

@@ -36,6 +36,23 @@ def test_static_scratch_sums_match_the_allocating_entry_point():
     assert not np.allclose(ref1, ref2)
 
 
+def test_static_scratch_sums_allocate_no_device_memory():
+    """What the entry point is for: once a context exists, calls leave the
+    device's free memory unchanged (read with cudaMemGetInfo), the first call
+    included (the scratch and the kernels are put in place when the context
+    is created)."""
+    import torch
+    g, o = make_pair(n=(60, 16, 32), nb=(12, 8, 8))
+    wind_setup(g, o)
+    ref = g.sums(0)
+    torch.cuda.synchronize()
+    free0, _ = torch.cuda.mem_get_info()
+    for _ in range(5):
+        assert _close(conservation_sums_static(g, 0), ref)
+    free1, _ = torch.cuda.mem_get_info()
+    assert free1 == free0, (free0, free1)
+
+
 def test_static_scratch_sums_on_a_refined_member_and_fp32():
     import math
     g, o = make_pair(n=(24, 16, 32), nb=(8, 8, 8), max_level=2, stretch=True, max_blocks=400,
