@@ -68,7 +68,7 @@ typedef enum {
 enum { ICARUS_FP64 = 0, ICARUS_FP32_MIXED = 1 };
 enum { ICARUS_SPHERICAL = 0, ICARUS_CARTESIAN = 1 };
 enum { ICARUS_BC_PERIODIC = 0, ICARUS_BC_OUTFLOW = 1, ICARUS_BC_REFLECT = 2, ICARUS_BC_INNER = 3 };
-enum { ICARUS_FLAG_PLAIN = 0, ICARUS_FLAG_LEARNED = 1, ICARUS_FLAG_BOTH = 2 };
+enum { ICARUS_FLAG_PLAIN = 0, ICARUS_FLAG_LEARNED = 1, ICARUS_FLAG_BOTH = 2, ICARUS_FLAG_SHOCK = 3 };
 
 /* Grid descriptor.
  *   n_cells      base-level cells (r, theta, phi); must be multiples of block.
@@ -116,17 +116,28 @@ typedef struct {
   double t_start, t_max, colat, lon, half_width, v, rho, p;
 } icarus_cone;
 
-/* Refinement criterion: Loehner second-derivative estimator E of density and
+/* Refinement criterion.
+ * ICARUS_FLAG_PLAIN: Loehner second-derivative estimator E of density and
  * pressure (diagonal form, index space, noise parameter eps).  A block is
  * flagged +1 (refine) if some interior cell has E > e_refine and
  * v_r > v_r,background + dv; -1 (coarsen) if no cell has E > e_coarsen with
- * that gate; 0 otherwise.  mode: ICARUS_FLAG_PLAIN, _LEARNED (plain flags,
- * set to +1 where the MLP pre-flagger's probability exceeds 1/2 on a block
- * below its member's finest level), _BOTH (both computed, plain flags
- * returned). */
+ * that gate; 0 otherwise.  _LEARNED: the plain flags, set to +1 where the
+ * MLP pre-flagger's probability exceeds 1/2 on a block below its member's
+ * finest level.  _BOTH: both computed, plain flags returned.
+ * ICARUS_FLAG_SHOCK (Sect. 3.2): a cell counts where the velocity divergence
+ * (central differences at cell centres, spherical form) is below -div_thr
+ * (the paper's criterion is div_thr = 0) and its centre lies within
+ * dlon_earth of Earth's longitude, within dcolat_earth of Earth's colatitude
+ * (see icarus_set_earth) and within dlon_cme of the member's CME longitude
+ * (the paper: 30, 10 and 90 degrees; a half width <= 0 switches that window
+ * off).  A block is flagged +1 if some interior cell counts, -1 (coarsen:
+ * the criterion no longer holds) otherwise.  Evaluated in FP64 with
+ * explicitly rounded operations.  ICARUS_ERR_ARG for div_thr < 0 or a half
+ * width >= pi.  The last five fields are read in the shock mode only. */
 typedef struct {
   double e_refine, e_coarsen, eps, dv;
   int mode;
+  double div_thr, dlon_earth, dcolat_earth, dlon_cme;
 } icarus_refine;
 
 /* Bytes of device arena that icarus_init_grid needs for this descriptor
@@ -236,6 +247,14 @@ icarus_status icarus_get_padded(icarus_ctx *ctx, int member, int leaf, double *h
 
 /* member time (host write / read) */
 icarus_status icarus_set_time(icarus_ctx *ctx, int member, double t);
+
+/* Earth's direction for the windows of the shock criterion (Sect. 3.2) of
+ * one member: colatitude colat and longitude lon0 - rate (t - t0) in the
+ * co-rotating frame, t the member's time (rate is the synodic rotation rate:
+ * Earth drifts against the rotation).  Windows that need Earth pass no cell
+ * until it is set.  Not stored in checkpoints.  ICARUS_ERR_ARG for a bad
+ * member or a non-finite value. */
+icarus_status icarus_set_earth(icarus_ctx *ctx, int member, double colat, double lon0, double t0, double rate);
 
 /* Per-member finest level (<= descriptor max_level). */
 icarus_status icarus_set_member_max_level(icarus_ctx *ctx, int member, int max_level);

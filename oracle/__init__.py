@@ -88,6 +88,9 @@ def lib():
                 "or_step": (V, [P, D]),
                 "or_advance": (I, [P, I, D]),
                 "or_flag": (V, [P, P, P]),
+                "or_set_earth": (V, [P, P]),
+                "or_flag_shock": (V, [P, P, P]),
+                "or_divv": (V, [P, I, P]),
                 "or_regrid": (V, [P, P]),
                 "or_probe": (V, [P, I, P, P]),
                 "or_sums": (V, [P, P]),
@@ -294,6 +297,25 @@ class Grid:
         crit = np.array([e_refine, e_coarsen, eps, dv], dtype=np.float64)
         out = np.zeros(self.nleaves, dtype=np.int8)
         lib().or_flag(self._g, _ptr(crit), _ptr(out))
+        return out
+
+    def set_earth(self, colat, lon0, t0=0.0, rate=0.0):
+        """Earth at colatitude colat, longitude lon0 - rate (t - t0)"""
+        e = np.array([colat, lon0, t0, rate], dtype=np.float64)
+        lib().or_set_earth(self._g, _ptr(e))
+
+    def flag_shock(self, div_thr=0.0, dlon_earth=np.radians(30.0), dcolat_earth=np.radians(10.0),
+                   dlon_cme=np.radians(90.0)):
+        """shock criterion (Sect. 3.2) after a ghost fill: +1 / -1 per leaf"""
+        crit = np.array([div_thr, dlon_earth, dcolat_earth, dlon_cme], dtype=np.float64)
+        out = np.zeros(self.nleaves, dtype=np.int8)
+        lib().or_flag_shock(self._g, _ptr(crit), _ptr(out))
+        return out
+
+    def divv(self, n):
+        """interior velocity divergence of leaf n (after a ghost fill)"""
+        out = np.zeros(self.nb)
+        lib().or_divv(self._g, n, _ptr(out))
         return out
 
     def regrid(self, flags):

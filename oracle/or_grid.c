@@ -855,6 +855,101 @@ void or_flag(or_grid *g, const double *crit, signed char *flags) {
   }
 }
 
+/* ------------------------------------------------------------------ */
+/* shock criterion (Sect. 3.2; reading R18)                            */
+/* ------------------------------------------------------------------ */
+/* e = {colat, lon0, t0, rate}: Earth at colatitude colat and longitude
+ * lon0 - rate (t - t0) in the co-rotating frame */
+void or_set_earth(or_grid *g, const double *e) {
+  g->earth.colat = e[0];
+  g->earth.lon0 = e[1];
+  g->earth.t0 = e[2];
+  g->earth.rate = e[3];
+  g->earth.set = 1;
+}
+
+/* divergence of the velocity v = m / rho at interior cell (a, c, e) of leaf
+ * b: central differences over the two neighbours in each direction, in the
+ * spherical form (1/r^2) d(r^2 v_r)/dr + (1/(r sin)) d(sin v_th)/dth +
+ * (1/(r sin)) dv_ph/dph with centre coordinates (Cartesian: plain central
+ * differences).  Needs one ghost layer. */
+static double divv_cell(or_grid *g, ob *b, int a, int c, int e) {
+  const int L = b->level, *nb = g->p.nb;
+  const int I = b->ix[0] * nb[0] + a, J = b->ix[1] * nb[1] + c, K = b->ix[2] * nb[2] + e;
+  const int i = a + NG, j = c + NG, k = e + NG;
+  const double *U = b->U;
+  double vrm = U[pidx(g, MR, i - 1, j, k)] / U[pidx(g, RHO, i - 1, j, k)];
+  double vrp = U[pidx(g, MR, i + 1, j, k)] / U[pidx(g, RHO, i + 1, j, k)];
+  double vtm = U[pidx(g, MT, i, j - 1, k)] / U[pidx(g, RHO, i, j - 1, k)];
+  double vtp = U[pidx(g, MT, i, j + 1, k)] / U[pidx(g, RHO, i, j + 1, k)];
+  double vpm = U[pidx(g, MP, i, j, k - 1)] / U[pidx(g, RHO, i, j, k - 1)];
+  double vpp = U[pidx(g, MP, i, j, k + 1)] / U[pidx(g, RHO, i, j, k + 1)];
+  double xm[3], x0[3], xp[3];
+  for (int d = 0; d < 3; d++) {
+    int Id = d == 0 ? I : (d == 1 ? J : K);
+    xm[d] = or_centre(g, L, d, Id - 1);
+    x0[d] = or_centre(g, L, d, Id);
+    xp[d] = or_centre(g, L, d, Id + 1);
+  }
+  double tr, tt, tp;
+  if (g->p.geometry == 0) {
+    double sm = sin(xm[1]), s0 = sin(x0[1]), sp = sin(xp[1]);
+    tr = ((xp[0] * xp[0]) * vrp - (xm[0] * xm[0]) * vrm) / ((x0[0] * x0[0]) * (xp[0] - xm[0]));
+    tt = (sp * vtp - sm * vtm) / ((x0[0] * s0) * (xp[1] - xm[1]));
+    tp = (vpp - vpm) / ((x0[0] * s0) * (xp[2] - xm[2]));
+  } else {
+    tr = (vrp - vrm) / (xp[0] - xm[0]);
+    tt = (vtp - vtm) / (xp[1] - xm[1]);
+    tp = (vpp - vpm) / (xp[2] - xm[2]);
+  }
+  return (tr + tt) + tp;
+}
+
+/* the interior velocity divergence of leaf n, [i][j][k] (after a ghost fill) */
+void or_divv(or_grid *g, int n, double *out) {
+  ob *b = g->leaves[n];
+  const int *nb = g->p.nb;
+  for (int a = 0; a < nb[0]; a++)
+    for (int c = 0; c < nb[1]; c++)
+      for (int e = 0; e < nb[2]; e++) out[((size_t)a * nb[1] + c) * nb[2] + e] = divv_cell(g, b, a, c, e);
+}
+
+/* angle a in [-pi, pi) */
+static double wrap_angle(double a) {
+  const double pi = 3.14159265358979323846, tp = 2.0 * pi;
+  return a - tp * floor((a + pi) / tp);
+}
+
+/* crit = {div_thr, dlon_earth, dcolat_earth, dlon_cme}: a cell counts where
+ * div v < -div_thr and its centre lies within dlon_earth of Earth's
+ * longitude, within dcolat_earth of Earth's colatitude and within dlon_cme of
+ * the CME's longitude (a half width <= 0 switches its window off; the Earth
+ * windows need or_set_earth, the CME window a CME).  A block is flagged +1
+ * when some interior cell counts and -1 (coarsen) otherwise: the paper
+ * refines where the criterion holds and coarsens once it no longer does.
+ * Needs ghost-filled U. */
+void or_flag_shock(or_grid *g, const double *crit, signed char *flags) {
+  const int *nb = g->p.nb;
+  const double lon_e = g->earth.lon0 - g->earth.rate * (g->t - g->earth.t0);
+  for (int n = 0; n < g->nleaves; n++) {
+    ob *b = g->leaves[n];
+    int L = b->level, refine = 0;
+    for (int a = 0; a < nb[0] && !refine; a++)
+      for (int c = 0; c < nb[1] && !refine; c++)
+        for (int e = 0; e < nb[2] && !refine; e++) {
+          int J = b->ix[1] * nb[1] + c, K = b->ix[2] * nb[2] + e;
+          double th = or_centre(g, L, 1, J), ph = or_centre(g, L, 2, K);
+          int in = 1;
+          if (crit[1] > 0.0) in = in && g->earth.set && fabs(wrap_angle(ph - lon_e)) <= crit[1];
+          if (crit[2] > 0.0) in = in && g->earth.set && fabs(th - g->earth.colat) <= crit[2];
+          if (crit[3] > 0.0) in = in && g->cme.active && fabs(wrap_angle(ph - g->cme.lon)) <= crit[3];
+          if (!in) continue;
+          if (divv_cell(g, b, a, c, e) < -crit[0]) refine = 1;
+        }
+    flags[n] = refine ? 1 : -1;
+  }
+}
+
 /* every leaf sharing a face, edge or corner with leaf b (periodic aware) */
 static int leaf_neighbours(or_grid *g, ob *b, ob **out, int cap) {
   int n = 0, L = b->level;

@@ -45,6 +45,11 @@ typedef struct {           /* cone CME, Eqs. 1-4; normalised units */
   int active;
 } or_cme;
 
+typedef struct {           /* Earth's direction for the shock windows (Sect. 3.2) */
+  double colat, lon0, t0, rate;   /* longitude lon0 - rate (t - t0), co-rotating */
+  int set;
+} or_earth;
+
 typedef struct ob ob;
 struct ob {
   int level;               /* 1 = base */
@@ -70,6 +75,7 @@ typedef struct {
   double *map;             /* inner boundary primitives [8][n1][n2] */
   double *vbg;             /* background v_r per base cell, or NULL */
   or_cme cme;
+  or_earth earth;
   double t;
   long floor_hits;
   int nthreads;

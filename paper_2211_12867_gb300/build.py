@@ -20,8 +20,10 @@ INCLUDE = os.path.join(os.path.dirname(HERE), "include")
 
 SOURCES = ["api.cu", "k_stage.cu", "k_ghost.cu", "k_amr.cu", "k_mlp.cu", "k_sums_static.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
+# host code without floating-point contraction: the geometry tables come out
+# bit for bit the same on every host architecture
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2",
-         "--expt-relaxed-constexpr"]
+         "-Xcompiler", "-ffp-contract=off", "--expt-relaxed-constexpr"]
 
 
 def nvcc() -> str:

@@ -41,7 +41,7 @@ struct Region {
 
 struct Layout {
   size_t total = 0;
-  Region geo, tables, blk, blk_alt, U, Us, Ualt, flux, lmap, lmap_off, bmap, cme, vbg, scal, flags, lists,
+  Region geo, tables, blk, blk_alt, U, Us, Ualt, flux, lmap, lmap_off, bmap, cme, earth, vbg, scal, flags, lists,
       sides, rlist, ops, shell, staging, partial, probe_in, probe_out, mlp_par, mlp_feat, mlp_X, mlp_T, mlp_idx,
       mlp_act, mlp_xin;
   size_t staging_doubles = 0, table_doubles = 0;
@@ -135,6 +135,7 @@ Layout make_layout(const icarus_grid_desc *d) {
   L.lmap_off = L.add((size_t)nm * (MAXLEV + 1) * sizeof(long long));
   L.bmap = L.add((size_t)nm * NVAR * d->n_cells[1] * d->n_cells[2] * sizeof(double));
   L.cme = L.add((size_t)nm * sizeof(DevCme));
+  L.earth = L.add((size_t)nm * sizeof(DevEarth));
   L.vbg = L.add((size_t)nm * d->n_cells[0] * d->n_cells[1] * d->n_cells[2] * sizeof(double));
   L.scal = L.add((size_t)nm * 7 * sizeof(double) + 64);
   L.flags = L.add(mb);
@@ -213,6 +214,7 @@ struct icarus_ctx {
   double *bmap = nullptr, *vbg = nullptr, *staging = nullptr, *partial = nullptr, *probe_in = nullptr,
          *probe_out = nullptr;
   DevCme *cme = nullptr;
+  DevEarth *earth = nullptr;
   double *t = nullptr, *dt_used = nullptr, *dt_cfl = nullptr, *tstop = nullptr, *updates = nullptr,
          *cells_m = nullptr;
   unsigned long long *inv_max = nullptr, *floor_hits = nullptr, *floor_prev = nullptr;
@@ -548,6 +550,7 @@ void fill_kp(icarus_ctx *c) {
   k.lmap_off = c->lmap_off;
   k.bmap = c->bmap;
   k.cme = c->cme;
+  k.earth = c->earth;
   k.vbg = c->vbg;
   k.t = c->t;
   k.dt_used = c->dt_used;
@@ -997,6 +1000,7 @@ icarus_status icarus_init_grid(const icarus_grid_desc *desc, icarus_ctx **out) {
   c->lmap_off = at<long long>(c, lay.lmap_off);
   c->bmap = at<double>(c, lay.bmap);
   c->cme = at<DevCme>(c, lay.cme);
+  c->earth = at<DevEarth>(c, lay.earth);
   c->vbg = at<double>(c, lay.vbg);
   double *sc = at<double>(c, lay.scal);
   const int nm = desc->n_members;
@@ -1053,6 +1057,7 @@ icarus_status icarus_init_grid(const icarus_grid_desc *desc, icarus_ctx **out) {
   // zero the small per-member and status words; the state pools are zeroed too
   if (cudaMemsetAsync(c->arena + lay.scal.off, 0, lay.scal.bytes, c->stream) != cudaSuccess ||
       cudaMemsetAsync(c->arena + lay.cme.off, 0, lay.cme.bytes, c->stream) != cudaSuccess ||
+      cudaMemsetAsync(c->arena + lay.earth.off, 0, lay.earth.bytes, c->stream) != cudaSuccess ||
       cudaMemsetAsync(c->arena + lay.bmap.off, 0, lay.bmap.bytes, c->stream) != cudaSuccess ||
       cudaMemsetAsync(c->arena + lay.U.off, 0, lay.U.bytes, c->stream) != cudaSuccess ||
       cudaMemsetAsync(c->arena + lay.Us.off, 0, lay.Us.bytes, c->stream) != cudaSuccess)
@@ -1155,6 +1160,16 @@ icarus_status icarus_set_time(icarus_ctx *c, int member, double t) {
   if (!member_ok(c, member)) return ICARUS_ERR_ARG;
   c->ghosts_fresh = false;
   CK(cudaMemcpyAsync(c->t + member, &t, sizeof(double), cudaMemcpyHostToDevice, c->stream));
+  CK(cudaStreamSynchronize(c->stream));
+  return ICARUS_OK;
+}
+
+icarus_status icarus_set_earth(icarus_ctx *c, int member, double colat, double lon0, double t0, double rate) {
+  if (!member_ok(c, member) || !std::isfinite(colat) || !std::isfinite(lon0) || !std::isfinite(t0) ||
+      !std::isfinite(rate))
+    return ICARUS_ERR_ARG;
+  const DevEarth e{colat, lon0, t0, rate, 1, 0};
+  CK(cudaMemcpyAsync(c->earth + member, &e, sizeof(DevEarth), cudaMemcpyHostToDevice, c->stream));
   CK(cudaStreamSynchronize(c->stream));
   return ICARUS_OK;
 }
@@ -1434,13 +1449,20 @@ icarus_status icarus_probe(icarus_ctx *c, int member, int n_pts, const double *r
 
 icarus_status icarus_flag_refine(icarus_ctx *c, const icarus_refine *crit, int8_t *flags_out) {
   if (!c || !crit) return ICARUS_ERR_ARG;
+  if (crit->mode < ICARUS_FLAG_PLAIN || crit->mode > ICARUS_FLAG_SHOCK) return ICARUS_ERR_ARG;
   if (c->poisoned) return ICARUS_ERR_STATE;
   if (!c->ghosts_fresh) {
     enqueue_ghost(c, c->U, 0.0);
     c->ghosts_fresh = true;
   }
-  estimator_launch(c->kp, c->U, c->prec, 0, c->nleaves, crit->e_refine, crit->e_coarsen, crit->eps, crit->dv,
-                   c->flags, c->stream);
+  if (crit->mode == ICARUS_FLAG_SHOCK) {
+    const double w[4] = {crit->div_thr, crit->dlon_earth, crit->dcolat_earth, crit->dlon_cme};
+    if (!(w[0] >= 0.0) || !(w[1] < M_PI) || !(w[2] < M_PI) || !(w[3] < M_PI)) return ICARUS_ERR_ARG;
+    shock_estimator_launch(c->kp, c->U, c->prec, 0, c->nleaves, w, c->flags, c->stream);
+  } else {
+    estimator_launch(c->kp, c->U, c->prec, 0, c->nleaves, crit->e_refine, crit->e_coarsen, crit->eps, crit->dv,
+                     c->flags, c->stream);
+  }
   if (crit->mode == ICARUS_FLAG_LEARNED) {
     if (!c->mlp_ready) return ICARUS_ERR_STATE;
     mlp_leaf_probabilities(c);

@@ -71,6 +71,13 @@ struct DevCme {
   int active, pad;
 };
 
+// Earth's direction for the windows of the shock criterion: colatitude and
+// longitude lon0 - rate (t - t0) in the co-rotating frame
+struct DevEarth {
+  double colat, lon0, t0, rate;
+  int set, pad;
+};
+
 // everything a kernel needs to know about the grid (passed by value)
 struct KParams {
   int nb[3], P[3];
@@ -86,6 +93,7 @@ struct KParams {
   const long long *lmap_off;   // [member * (MAXLEV+1) + L]
   const double *bmap;          // [member][8][n1][n2] inner boundary primitives
   const DevCme *cme;           // [member]
+  const DevEarth *earth;       // [member]
   const double *vbg;           // [member][n0][n1][n2] background v_r
   double *t;                   // [member]
   double *dt_used;             // [member]
@@ -141,6 +149,9 @@ void unpack_state_launch(const KParams &kp, void *U, int precision, int slot0, i
                          int is_prim, cudaStream_t s);
 void estimator_launch(const KParams &kp, const void *U, int precision, int slot0, int nslots, double e_ref,
                       double e_crs, double eps, double dv, signed char *flags, cudaStream_t s);
+// shock criterion: crit = {div_thr, dlon_earth, dcolat_earth, dlon_cme}
+void shock_estimator_launch(const KParams &kp, const void *U, int precision, int slot0, int nslots,
+                            const double *crit, signed char *flags, cudaStream_t s);
 struct MoveOp {       // one new leaf of a regrid
   int kind;           // 0 copy, 1 prolong from the old parent, 2 restrict from 8 old children
   int dst;            // new slot

@@ -129,6 +129,71 @@ __global__ void k_estimator(const KParams kp, const real *U, int slot0, double e
   if (threadIdx.x == 0) flags[blockIdx.x] = refine ? 1 : (keep ? 0 : -1);
 }
 
+// ---- shock criterion (Sect. 3.2) ----
+// The paper refines where the velocity divergence is negative, inside
+// windows around the Sun-Earth line and the CME's hemisphere, and coarsens
+// once the criterion fails.  The divergence is the central difference at cell
+// centres in spherical form; everything is FP64 with explicitly rounded
+// operations in a fixed order, so the flags agree bit for bit with any IEEE
+// FP64 evaluation of the same expression on the same stored state and
+// geometry.
+__device__ __forceinline__ double wrap_pi(double a) {
+  const double pi = 3.14159265358979323846, tp = 2.0 * pi;
+  return __dsub_rn(a, __dmul_rn(tp, floor(__ddiv_rn(__dadd_rn(a, pi), tp))));
+}
+
+template <typename real>
+__device__ __forceinline__ double vel(const KParams &kp, const real *U, int slot, int v, int p0, int p1, int p2) {
+  return __ddiv_rn((double)U[cidx<real>(kp, slot, v, p0, p1, p2)], (double)U[cidx<real>(kp, slot, 0, p0, p1, p2)]);
+}
+
+template <typename real>
+__global__ void k_shock_estimator(const KParams kp, const real *U, int slot0, double div_thr, double w_le,
+                                  double w_ce, double w_lc, signed char *flags) {
+  const int slot = slot0 + blockIdx.x;
+  const DevBlock B = kp.blk[slot];
+  const LevelGeo<double> &G = kp.geo->d[B.level];
+  const DevEarth E = kp.earth[B.member];
+  const DevCme C = kp.cme[B.member];
+  const double t = kp.t[B.member];
+  const double lon_e = __dsub_rn(E.lon0, __dmul_rn(E.rate, __dsub_rn(t, E.t0)));
+  const bool sph = kp.geometry == 0;
+  int refine = 0;
+  for (int c = threadIdx.x; c < kp.icells && !refine; c += blockDim.x) {
+    const int k = c % kp.nb[2], j = (c / kp.nb[2]) % kp.nb[1], i = c / (kp.nb[2] * kp.nb[1]);
+    const int I = B.ix[0] * kp.nb[0] + i + NGH, J = B.ix[1] * kp.nb[1] + j + NGH, K = B.ix[2] * kp.nb[2] + k + NGH;
+    const double th = G.tc[J], ph = G.pc[K];
+    bool in = true;
+    if (w_le > 0.0) in = in && E.set && fabs(wrap_pi(__dsub_rn(ph, lon_e))) <= w_le;
+    if (w_ce > 0.0) in = in && E.set && fabs(__dsub_rn(th, E.colat)) <= w_ce;
+    if (w_lc > 0.0) in = in && C.active && fabs(wrap_pi(__dsub_rn(ph, C.lon))) <= w_lc;
+    if (!in) continue;
+    const int p0 = i + NGH, p1 = j + NGH, p2 = k + NGH;
+    const double vrm = vel(kp, U, slot, 1, p0 - 1, p1, p2), vrp = vel(kp, U, slot, 1, p0 + 1, p1, p2);
+    const double vtm = vel(kp, U, slot, 2, p0, p1 - 1, p2), vtp = vel(kp, U, slot, 2, p0, p1 + 1, p2);
+    const double vpm = vel(kp, U, slot, 3, p0, p1, p2 - 1), vpp = vel(kp, U, slot, 3, p0, p1, p2 + 1);
+    const double rm = G.rc[I - 1], r0 = G.rc[I], rp = G.rc[I + 1];
+    const double tm = G.tc[J - 1], tp = G.tc[J + 1], qm = G.pc[K - 1], qp = G.pc[K + 1];
+    double a, b, e;
+    if (sph) {
+      const double sm = G.sintc[J - 1], s0 = G.sintc[J], sp = G.sintc[J + 1];
+      a = __ddiv_rn(__dsub_rn(__dmul_rn(__dmul_rn(rp, rp), vrp), __dmul_rn(__dmul_rn(rm, rm), vrm)),
+                    __dmul_rn(__dmul_rn(r0, r0), __dsub_rn(rp, rm)));
+      const double rs = __dmul_rn(r0, s0);
+      b = __ddiv_rn(__dsub_rn(__dmul_rn(sp, vtp), __dmul_rn(sm, vtm)), __dmul_rn(rs, __dsub_rn(tp, tm)));
+      e = __ddiv_rn(__dsub_rn(vpp, vpm), __dmul_rn(rs, __dsub_rn(qp, qm)));
+    } else {
+      a = __ddiv_rn(__dsub_rn(vrp, vrm), __dsub_rn(rp, rm));
+      b = __ddiv_rn(__dsub_rn(vtp, vtm), __dsub_rn(tp, tm));
+      e = __ddiv_rn(__dsub_rn(vpp, vpm), __dsub_rn(qp, qm));
+    }
+    const double div = __dadd_rn(__dadd_rn(a, b), e);
+    if (div < -div_thr) refine = 1;
+  }
+  refine = __syncthreads_or(refine);
+  if (threadIdx.x == 0) flags[blockIdx.x] = refine ? 1 : -1;
+}
+
 // ---- regrid data movement ----
 template <typename real>
 __device__ void prolong_child(const KParams &kp, const real *U, int cs, const int *Ic, int ch, real *out) {
@@ -373,6 +438,17 @@ void estimator_launch(const KParams &kp, const void *U, int precision, int slot0
     k_estimator<float><<<nslots, 256, 0, s>>>(kp, (const float *)U, slot0, e_ref, e_crs, eps, dv, flags);
   else
     k_estimator<double><<<nslots, 256, 0, s>>>(kp, (const double *)U, slot0, e_ref, e_crs, eps, dv, flags);
+}
+
+void shock_estimator_launch(const KParams &kp, const void *U, int precision, int slot0, int nslots,
+                            const double *crit, signed char *flags, cudaStream_t s) {
+  if (nslots <= 0) return;
+  if (precision)
+    k_shock_estimator<float><<<nslots, 256, 0, s>>>(kp, (const float *)U, slot0, crit[0], crit[1], crit[2], crit[3],
+                                                     flags);
+  else
+    k_shock_estimator<double><<<nslots, 256, 0, s>>>(kp, (const double *)U, slot0, crit[0], crit[1], crit[2],
+                                                      crit[3], flags);
 }
 
 void regrid_move_launch2(const KParams &kp_old, const void *Uold, void *Unew, const DevBlock *nblk, int precision,

@@ -22,7 +22,10 @@ _lib = None
 FP64, FP32_MIXED = 0, 1
 SPHERICAL, CARTESIAN = 0, 1
 BC_PERIODIC, BC_OUTFLOW, BC_REFLECT, BC_INNER = 0, 1, 2, 3
-FLAG_PLAIN, FLAG_LEARNED, FLAG_BOTH = 0, 1, 2
+FLAG_PLAIN, FLAG_LEARNED, FLAG_BOTH, FLAG_SHOCK = 0, 1, 2, 3
+# the shock criterion's windows of the paper (Sect. 3.2): Earth longitude
+# +-30 deg, Earth colatitude +-10 deg, CME longitude +-90 deg
+SHOCK_WINDOWS = (math.radians(30.0), math.radians(10.0), math.radians(90.0))
 
 STATUS = {0: "ok", 1: "invalid argument", 2: "arena too small", 3: "CUDA error",
           4: "non-physical state", 5: "device wait timed out", 6: "call out of order",
@@ -35,7 +38,7 @@ EXPORTS = [
     "icarus_set_member_max_level", "icarus_ghost_fill", "icarus_conservation_sums", "icarus_get_dt",
     "icarus_status_word", "icarus_set_tile", "icarus_use_graph", "icarus_kernels_per_step",
     "icarus_profile", "icarus_profile_read", "icarus_set_fp64_islands", "icarus_conservation_sums_static",
-    "icarus_set_floor_budget", "icarus_get_padded",
+    "icarus_set_floor_budget", "icarus_get_padded", "icarus_set_earth",
     "icarus_mlp_set_params", "icarus_mlp_get_params", "icarus_mlp_features", "icarus_mlp_predict_leaves",
     "icarus_mlp_predict", "icarus_mlp_grad", "icarus_mlp_dataset_clear", "icarus_mlp_dataset_add",
     "icarus_mlp_train", "icarus_cell_updates", "icarus_save", "icarus_load", "icarus_destroy",
@@ -68,7 +71,9 @@ class Cone(C.Structure):
 
 class Refine(C.Structure):
     _fields_ = [("e_refine", C.c_double), ("e_coarsen", C.c_double), ("eps", C.c_double),
-                ("dv", C.c_double), ("mode", C.c_int)]
+                ("dv", C.c_double), ("mode", C.c_int),
+                ("div_thr", C.c_double), ("dlon_earth", C.c_double), ("dcolat_earth", C.c_double),
+                ("dlon_cme", C.c_double)]
 
 
 def load(build_if_missing: bool = True):
@@ -229,8 +234,9 @@ class Icarus:
                                                  _dp(out) if want_time else None))
         return out
 
-    def flag_refine(self, e_refine=0.1, e_coarsen=0.0125, eps=0.01, dv=0.5, mode=FLAG_PLAIN):
-        crit = Refine(e_refine, e_coarsen, eps, dv, mode)
+    def flag_refine(self, e_refine=0.1, e_coarsen=0.0125, eps=0.01, dv=0.5, mode=FLAG_PLAIN, div_thr=0.0,
+                    windows=SHOCK_WINDOWS):
+        crit = Refine(e_refine, e_coarsen, eps, dv, mode, div_thr, *windows)
         out = np.zeros(self.n_leaves(-1), dtype=np.int8)
         _chk("icarus_flag_refine", self.lib.icarus_flag_refine(self.ctx, C.byref(crit),
                                                                out.ctypes.data_as(C.c_void_p)))
@@ -269,6 +275,13 @@ class Icarus:
 
     def set_time(self, member, t):
         _chk("icarus_set_time", self.lib.icarus_set_time(self.ctx, member, float(t)))
+
+    def set_earth(self, member, colat, lon0, t0=0.0, rate=0.0):
+        """Earth at colatitude colat, longitude lon0 - rate (t - t0) (shock windows)"""
+        f = self.lib.icarus_set_earth
+        f.restype = C.c_int
+        f.argtypes = [C.c_void_p, C.c_int, C.c_double, C.c_double, C.c_double, C.c_double]
+        _chk("icarus_set_earth", f(self.ctx, member, float(colat), float(lon0), float(t0), float(rate)))
 
     def set_member_max_level(self, member, level):
         _chk("icarus_set_member_max_level", self.lib.icarus_set_member_max_level(self.ctx, member, level))
