@@ -52,7 +52,7 @@ class Params(C.Structure):
         ("xmin", C.c_double * 3), ("xmax", C.c_double * 3),
         ("gamma", C.c_double), ("omega", C.c_double), ("cfl", C.c_double),
         ("divb_cd", C.c_double), ("bc_lo", C.c_int * 3), ("bc_hi", C.c_int * 3),
-        ("p_floor", C.c_double), ("rho_floor", C.c_double),
+        ("p_floor", C.c_double), ("rho_floor", C.c_double), ("tracer", C.c_int),
     ]
 
 
@@ -91,6 +91,9 @@ def lib():
                 "or_set_earth": (V, [P, P]),
                 "or_flag_shock": (V, [P, P, P]),
                 "or_divv": (V, [P, I, P]),
+                "or_get_tracer": (V, [P, P]),
+                "or_set_tracer": (V, [P, P]),
+                "or_flag_tracer": (V, [P, P, P]),
                 "or_regrid": (V, [P, P]),
                 "or_probe": (V, [P, I, P, P]),
                 "or_sums": (V, [P, P]),
@@ -181,7 +184,7 @@ class Grid:
                  gamma=1.5, omega=0.0, cfl=0.8, divb_cd=0.8,
                  bc_lo=(BC_INNER, BC_OUTFLOW, BC_PERIODIC),
                  bc_hi=(BC_OUTFLOW, BC_OUTFLOW, BC_PERIODIC),
-                 p_floor=1e-8, rho_floor=1e-8, threads=0):
+                 p_floor=1e-8, rho_floor=1e-8, tracer=0, threads=0):
         p = Params()
         p.geometry = geometry
         p.n[:] = list(n)
@@ -194,6 +197,7 @@ class Grid:
         p.bc_lo[:] = list(bc_lo)
         p.bc_hi[:] = list(bc_hi)
         p.p_floor, p.rho_floor = p_floor, rho_floor
+        p.tracer = int(bool(tracer))
         self.params = p
         self.n, self.nb, self.gamma = tuple(n), tuple(nb), gamma
         self.max_level = max_level
@@ -310,6 +314,24 @@ class Grid:
         crit = np.array([div_thr, dlon_earth, dcolat_earth, dlon_cme], dtype=np.float64)
         out = np.zeros(self.nleaves, dtype=np.int8)
         lib().or_flag_shock(self._g, _ptr(crit), _ptr(out))
+        return out
+
+    def get_tracer(self):
+        """rho X of the interior cells, [leaf][i][j][k]"""
+        out = np.zeros((self.nleaves,) + self.nb)
+        lib().or_get_tracer(self._g, _ptr(out))
+        return out
+
+    def set_tracer(self, T):
+        T = np.ascontiguousarray(T, dtype=np.float64).reshape((self.nleaves,) + self.nb)
+        lib().or_set_tracer(self._g, _ptr(T))
+
+    def flag_tracer(self, x_thr=0.0, div_thr=0.0, dlon_earth=0.0, dcolat_earth=0.0, dlon_cme=0.0,
+                    combined=False):
+        """tracer criterion (Sect. 3.1) or, combined, tracer or shock (Sect. 3.3)"""
+        crit = np.array([x_thr, div_thr, dlon_earth, dcolat_earth, dlon_cme, 1.0 if combined else 0.0])
+        out = np.zeros(self.nleaves, dtype=np.int8)
+        lib().or_flag_tracer(self._g, _ptr(crit), _ptr(out))
         return out
 
     def divv(self, n):

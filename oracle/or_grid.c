@@ -140,7 +140,7 @@ static int face_ncells(const or_grid *g, int d) {
 }
 
 static void alloc_block_data(or_grid *g, ob *b) {
-  size_t n = or_pcells(g) * NV;
+  size_t n = or_pcells(g) * NVT;
   b->U = calloc(n, sizeof(double));
   b->Us = calloc(n, sizeof(double));
   for (int f = 0; f < 6; f++) b->fx[f] = calloc((size_t)face_ncells(g, f / 2) * NV, sizeof(double));
@@ -253,11 +253,11 @@ static inline double *buf(ob *b, int which) { return which ? b->Us : b->U; }
  * slope of the conserved variables; if any child has p <= 0 or rho <= 0 all
  * children take U_p. */
 static void prolong_children(const or_grid *g, ob *cb, int which, const int pc[3],
-                             const int Ic[3], double out[8][NV]) {
+                             const int Ic[3], double out[8][NVT]) {
   double *A = buf(cb, which);
   int Lc = cb->level;
-  double s[3][NV], up[NV];
-  for (int v = 0; v < NV; v++) {
+  double s[3][NVT], up[NVT];
+  for (int v = 0; v < NVT; v++) {
     up[v] = A[pidx(g, v, pc[0], pc[1], pc[2])];
     for (int d = 0; d < 3; d++) {
       int m[3] = {pc[0], pc[1], pc[2]}, p[3] = {pc[0], pc[1], pc[2]};
@@ -271,7 +271,7 @@ static void prolong_children(const or_grid *g, ob *cb, int which, const int pc[3
     int o[3] = {(ch >> 2) & 1, (ch >> 1) & 1, ch & 1};
     double dl[3];
     for (int d = 0; d < 3; d++) dl[d] = g->dlt[d][Lc][2 * Ic[d] + o[d]];
-    for (int v = 0; v < NV; v++)
+    for (int v = 0; v < NVT; v++)
       out[ch][v] = ((up[v] + s[0][v] * dl[0]) + s[1][v] * dl[1]) + s[2][v] * dl[2];
     double W[NV];
     or_cons2prim(out[ch], W, g->p.gamma);
@@ -279,7 +279,7 @@ static void prolong_children(const or_grid *g, ob *cb, int which, const int pc[3
   }
   if (!ok)
     for (int ch = 0; ch < 8; ch++)
-      for (int v = 0; v < NV; v++) out[ch][v] = up[v];
+      for (int v = 0; v < NVT; v++) out[ch][v] = up[v];
 }
 
 /* prolonged value of fine cell (Lf, I, J, K) from coarse leaf cb */
@@ -287,17 +287,17 @@ static void prolong_cell(const or_grid *g, ob *cb, int which, int I, int J, int 
   int Ic[3] = {I >> 1, J >> 1, K >> 1};
   int pc[3];
   for (int d = 0; d < 3; d++) pc[d] = Ic[d] - cb->ix[d] * g->p.nb[d] + NG;
-  double ch[8][NV];
+  double ch[8][NVT];
   prolong_children(g, cb, which, pc, Ic, ch);
   int c = ((I & 1) << 2) | ((J & 1) << 1) | (K & 1);
-  memcpy(out, ch[c], sizeof(double) * NV);
+  memcpy(out, ch[c], sizeof(double) * NVT);
 }
 
 static int wrap(const or_grid *g, int L, int d, int I, int *inside);
 
 /* volume-weighted mean of the 8 level-(L+1) cells under cell (L, I, J, K) */
 static void restrict_cell(const or_grid *g, int which, int L, int I, int J, int K, double *out) {
-  double sum[NV] = {0}, vs = 0.0;
+  double sum[NVT] = {0}, vs = 0.0;
   for (int a = 0; a < 2; a++)
     for (int b = 0; b < 2; b++)
       for (int c = 0; c < 2; c++) {
@@ -315,10 +315,10 @@ static void restrict_cell(const or_grid *g, int which, int L, int I, int J, int 
         int p0 = cI - fb->ix[0] * g->p.nb[0] + NG;
         int p1 = cJ - fb->ix[1] * g->p.nb[1] + NG;
         int p2 = wK - fb->ix[2] * g->p.nb[2] + NG;
-        for (int v = 0; v < NV; v++) sum[v] += V * A[pidx(g, v, p0, p1, p2)];
+        for (int v = 0; v < NVT; v++) sum[v] += V * A[pidx(g, v, p0, p1, p2)];
         vs += V;
       }
-  for (int v = 0; v < NV; v++) out[v] = sum[v] / vs;
+  for (int v = 0; v < NVT; v++) out[v] = sum[v] / vs;
 }
 
 /* ------------------------------------------------------------------ */
@@ -355,12 +355,12 @@ static void fill_neighbour_ghosts(or_grid *g, ob *b, int which) {
         if (!in) continue;
         int lev;
         ob *o = find_cover(g, L, G[0], G[1], G[2], &lev);
-        double val[NV];
+        double val[NVT];
         if (lev == L && o->is_leaf) {
           double *B = buf(o, which);
           int q[3];
           for (int d = 0; d < 3; d++) q[d] = G[d] - o->ix[d] * g->p.nb[d] + NG;
-          for (int v = 0; v < NV; v++) val[v] = B[pidx(g, v, q[0], q[1], q[2])];
+          for (int v = 0; v < NVT; v++) val[v] = B[pidx(g, v, q[0], q[1], q[2])];
         } else if (lev == L - 1) {
           prolong_cell(g, o, which, G[0], G[1], G[2], val);
         } else if (lev == L) {
@@ -369,7 +369,7 @@ static void fill_neighbour_ghosts(or_grid *g, ob *b, int which) {
           fprintf(stderr, "oracle: 2:1 balance violated in ghost fill\n");
           abort();
         }
-        for (int v = 0; v < NV; v++) A[pidx(g, v, i, j, k)] = val[v];
+        for (int v = 0; v < NVT; v++) A[pidx(g, v, i, j, k)] = val[v];
       }
 }
 
@@ -377,7 +377,7 @@ static void fill_neighbour_ghosts(or_grid *g, ob *b, int which) {
  * (not rescaled in r, reading R13), overlaid by the cone CME where d <= theta(t)
  * (Eqs. 1-4).  CME plasma: v_r = v_CME, v_ph = -Omega r_in sin(theta), B = 0. */
 static void inner_state(const or_grid *g, int L, int J, int K, double t, double *U) {
-  double W[NV];
+  double W[NV], X = 0.0;
   int jb = J >> (L - 1), kb = K >> (L - 1);
   int n1 = g->p.n[1], n2 = g->p.n[2];
   for (int v = 0; v < NV; v++) W[v] = g->map[((size_t)v * n1 + jb) * n2 + kb];
@@ -391,8 +391,10 @@ static void inner_state(const or_grid *g, int L, int J, int K, double t, double 
     W[3] = -g->p.omega * R * sin(th);
     W[EN] = g->cme.p;
     W[5] = W[6] = W[7] = 0.0;
+    X = 1.0;   /* CME plasma carries the tracer (Sect. 3.1) */
   }
   or_prim2cons(W, U, g->p.gamma);
+  U[TR] = W[RHO] * X;
 }
 
 static void fill_physical_ghosts(or_grid *g, ob *b, int which, double t) {
@@ -424,13 +426,13 @@ static void fill_physical_ghosts(or_grid *g, ob *b, int which, double t) {
               int J = wrap(g, L, 1, b->ix[1] * g->p.nb[1] + q[1] - NG, &ins1);
               int K = wrap(g, L, 2, b->ix[2] * g->p.nb[2] + q[2] - NG, &ins2);
               if (!ins1 || !ins2) continue;
-              double U[NV];
+              double U[NVT];
               inner_state(g, L, J, K, t, U);
-              for (int v = 0; v < NV; v++) A[pidx(g, v, q[0], q[1], q[2])] = U[v];
+              for (int v = 0; v < NVT; v++) A[pidx(g, v, q[0], q[1], q[2])] = U[v];
               continue;
             }
             s[d] = bc == BC_REFLECT ? pm : pn;
-            for (int v = 0; v < NV; v++) {
+            for (int v = 0; v < NVT; v++) {
               double x = A[pidx(g, v, s[0], s[1], s[2])];
               if (bc == BC_REFLECT && (v == 1 + d || v == 5 + d)) x = -x;
               A[pidx(g, v, q[0], q[1], q[2])] = x;
@@ -645,6 +647,24 @@ static long stage_block(or_grid *g, ob *b, int in_which, double dtf, int clean, 
         hits += apply_floors(g, un);
         double *Out = in_which == 0 ? b->Us : b->U;
         for (int v = 0; v < NV; v++) Out[pidx(g, v, i, j, k)] = un[v];
+        if (g->p.tracer) {
+          /* CME tracer (Sect. 3.1; reading R19): rho X carried by the mass
+           * flux of each face with X taken from the face's upwind cell */
+          double fl[3][2];
+          size_t oo[3][2] = {{o0lo, o0hi}, {o1lo, o1hi}, {o2lo, o2hi}};
+          for (int d = 0; d < 3; d++)
+            for (int h = 0; h < 2; h++) {
+              int lo[3] = {i, j, k}, hi3[3] = {i, j, k};
+              if (h) hi3[d]++;
+              else lo[d]--;
+              double F = AF[d][oo[d][h] + RHO];
+              double Xl = Uin[pidx(g, TR, lo[0], lo[1], lo[2])] / Uin[pidx(g, RHO, lo[0], lo[1], lo[2])];
+              double Xh = Uin[pidx(g, TR, hi3[0], hi3[1], hi3[2])] / Uin[pidx(g, RHO, hi3[0], hi3[1], hi3[2])];
+              fl[d][h] = F * (F > 0.0 ? Xl : Xh);
+            }
+          double dT = -((fl[0][1] - fl[0][0]) + (fl[1][1] - fl[1][0]) + (fl[2][1] - fl[2][0])) / V;
+          Out[pidx(g, TR, i, j, k)] = U0[pidx(g, TR, i, j, k)] + dtf * dT;
+        }
       }
   if (store_flux) {
     for (int f = 0; f < 6; f++) {
@@ -950,6 +970,61 @@ void or_flag_shock(or_grid *g, const double *crit, signed char *flags) {
   }
 }
 
+/* ------------------------------------------------------------------ */
+/* CME tracer (Sect. 3.1) and combined criterion (Sect. 3.3)           */
+/* ------------------------------------------------------------------ */
+/* rho X of every leaf's interior cells, [leaf][i][j][k] */
+void or_get_tracer(or_grid *g, double *out) {
+  const int *nb = g->p.nb;
+  size_t bc = (size_t)nb[0] * nb[1] * nb[2];
+  for (int n = 0; n < g->nleaves; n++)
+    for (int a = 0; a < nb[0]; a++)
+      for (int c = 0; c < nb[1]; c++)
+        for (int e = 0; e < nb[2]; e++)
+          out[n * bc + ((size_t)a * nb[1] + c) * nb[2] + e] = g->leaves[n]->U[pidx(g, TR, a + NG, c + NG, e + NG)];
+}
+
+void or_set_tracer(or_grid *g, const double *in) {
+  const int *nb = g->p.nb;
+  size_t bc = (size_t)nb[0] * nb[1] * nb[2];
+  for (int n = 0; n < g->nleaves; n++)
+    for (int a = 0; a < nb[0]; a++)
+      for (int c = 0; c < nb[1]; c++)
+        for (int e = 0; e < nb[2]; e++)
+          g->leaves[n]->U[pidx(g, TR, a + NG, c + NG, e + NG)] = in[n * bc + ((size_t)a * nb[1] + c) * nb[2] + e];
+}
+
+/* crit = {x_thr, div_thr, dlon_earth, dcolat_earth, dlon_cme, combined}: a
+ * cell counts where its tracer fraction X = rho X / rho exceeds x_thr (the
+ * paper refines where X is non-zero: x_thr = 0), or, when combined != 0,
+ * also where div v < -div_thr (Sect. 3.3); the windows are those of the
+ * shock criterion (a half width <= 0 switches one off).  +1 where some
+ * interior cell counts, -1 otherwise.  Needs ghost-filled U (for div v). */
+void or_flag_tracer(or_grid *g, const double *crit, signed char *flags) {
+  const int *nb = g->p.nb;
+  const double lon_e = g->earth.lon0 - g->earth.rate * (g->t - g->earth.t0);
+  for (int n = 0; n < g->nleaves; n++) {
+    ob *b = g->leaves[n];
+    int L = b->level, refine = 0;
+    for (int a = 0; a < nb[0] && !refine; a++)
+      for (int c = 0; c < nb[1] && !refine; c++)
+        for (int e = 0; e < nb[2] && !refine; e++) {
+          int J = b->ix[1] * nb[1] + c, K = b->ix[2] * nb[2] + e;
+          double th = or_centre(g, L, 1, J), ph = or_centre(g, L, 2, K);
+          int in = 1;
+          if (crit[2] > 0.0) in = in && g->earth.set && fabs(wrap_angle(ph - lon_e)) <= crit[2];
+          if (crit[3] > 0.0) in = in && g->earth.set && fabs(th - g->earth.colat) <= crit[3];
+          if (crit[4] > 0.0) in = in && g->cme.active && fabs(wrap_angle(ph - g->cme.lon)) <= crit[4];
+          if (!in) continue;
+          int i = a + NG, j = c + NG, k = e + NG;
+          double X = b->U[pidx(g, TR, i, j, k)] / b->U[pidx(g, RHO, i, j, k)];
+          if (X > crit[0]) refine = 1;
+          else if (crit[5] != 0.0 && divv_cell(g, b, a, c, e) < -crit[1]) refine = 1;
+        }
+    flags[n] = refine ? 1 : -1;
+  }
+}
+
 /* every leaf sharing a face, edge or corner with leaf b (periodic aware) */
 static int leaf_neighbours(or_grid *g, ob *b, ob **out, int cap) {
   int n = 0, L = b->level;
@@ -994,7 +1069,7 @@ static void refine_block(or_grid *g, ob *b) {
       for (int e = 0; e < nb[2]; e++) {
         int pc[3] = {a + NG, c + NG, e + NG};
         int Ic[3] = {b->ix[0] * nb[0] + a, b->ix[1] * nb[1] + c, b->ix[2] * nb[2] + e};
-        double kids[8][NV];
+        double kids[8][NVT];
         prolong_children(g, b, 0, pc, Ic, kids);
         for (int ch = 0; ch < 8; ch++) {
           int o[3] = {(ch >> 2) & 1, (ch >> 1) & 1, ch & 1};
@@ -1005,7 +1080,7 @@ static void refine_block(or_grid *g, ob *b) {
           ob *kid = b->child[(cb[0] << 2) | (cb[1] << 1) | cb[2]];
           int q[3];
           for (int d = 0; d < 3; d++) q[d] = F[d] - kid->ix[d] * nb[d] + NG;
-          for (int v = 0; v < NV; v++) kid->U[pidx(g, v, q[0], q[1], q[2])] = kids[ch][v];
+          for (int v = 0; v < NVT; v++) kid->U[pidx(g, v, q[0], q[1], q[2])] = kids[ch][v];
         }
       }
   free_block_data(b);
@@ -1021,7 +1096,7 @@ static void coarsen_block(or_grid *g, ob *b) {
     for (int c = 0; c < nb[1]; c++)
       for (int e = 0; e < nb[2]; e++) {
         int I = b->ix[0] * nb[0] + a, J = b->ix[1] * nb[1] + c, K = b->ix[2] * nb[2] + e;
-        double sum[NV] = {0}, vs = 0.0;
+        double sum[NVT] = {0}, vs = 0.0;
         for (int x = 0; x < 2; x++)
           for (int y = 0; y < 2; y++)
             for (int z = 0; z < 2; z++) {
@@ -1032,10 +1107,10 @@ static void coarsen_block(or_grid *g, ob *b) {
               int q[3];
               for (int d = 0; d < 3; d++) q[d] = F[d] - kid->ix[d] * nb[d] + NG;
               double V = cell_volume(g, b->level + 1, F[0], F[1], F[2]);
-              for (int v = 0; v < NV; v++) sum[v] += V * kid->U[pidx(g, v, q[0], q[1], q[2])];
+              for (int v = 0; v < NVT; v++) sum[v] += V * kid->U[pidx(g, v, q[0], q[1], q[2])];
               vs += V;
             }
-        for (int v = 0; v < NV; v++) b->U[pidx(g, v, a + NG, c + NG, e + NG)] = sum[v] / vs;
+        for (int v = 0; v < NVT; v++) b->U[pidx(g, v, a + NG, c + NG, e + NG)] = sum[v] / vs;
       }
   for (int c = 0; c < 8; c++) {
     free_block_data(b->child[c]);

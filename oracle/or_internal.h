@@ -14,7 +14,9 @@
  *              absorbed (normalised units of the grid descriptor).
  *   direction  0 = r (index i), 1 = theta (j), 2 = phi (k); Cartesian mode
  *              uses the same slots for x, y, z.
- *   blocks     padded with NG = 2 ghost layers; storage [v][i][j][k].
+ *   blocks     padded with NG = 2 ghost layers; storage [v][i][j][k] with
+ *              v = 0..7 the MHD variables and v = TR the CME tracer rho X
+ *              (zero unless the tracer is on).
  */
 #ifndef OR_INTERNAL_H
 #define OR_INTERNAL_H
@@ -22,6 +24,8 @@
 #include <stdint.h>
 
 #define NV 8
+#define NVT 9   /* storage per cell: the 8 MHD variables and the CME tracer rho X */
+#define TR 8    /* index of the tracer in a block's storage */
 #define NG 2
 #define OR_MAXL 8
 
@@ -38,6 +42,7 @@ typedef struct {
   double gamma, omega, cfl, divb_cd;
   int bc_lo[3], bc_hi[3];
   double p_floor, rho_floor;
+  int tracer;              /* 1: advect the CME density tracer (Sect. 3.1) */
 } or_params;
 
 typedef struct {           /* cone CME, Eqs. 1-4; normalised units */
@@ -57,7 +62,7 @@ struct ob {
   ob *parent;
   ob *child[8];            /* child c = (a<<2)|(b<<1)|c3 for offsets a,b,c3 */
   int is_leaf;
-  double *U, *Us;          /* padded state and stage state */
+  double *U, *Us;          /* padded state and stage state, NVT variables */
   double *fx[6];           /* area x flux on faces (lo/hi per dir), [cell][v] */
   int nbr_level[6];        /* level of face-neighbour region owner (0 = boundary) */
   signed char flag;
