@@ -165,9 +165,11 @@ def setup_grid(precision, seed=0):
     return g, W, wm, cme
 
 
-def roofline_traffic(prec_tag):
-    """DRAM traffic per corrector launch (dram__bytes_read + write) from the
-    committed ncu summary, if it was taken on the current stage-kernel
+def profile_figure(prec_tag, key):
+    """A per-launch figure of the corrector (`traffic_bytes_per_launch`:
+    dram__bytes_read + write; `warp_inst_per_launch`: inst_executed;
+    `fp64_flop_per_launch`: 2 x DFMA + DADD + DMUL thread instructions) from
+    the committed ncu summary, if it was taken on the current stage-kernel
     source and precision; None otherwise."""
     path = os.path.join(ROOT, "profiles", f"k_stage_corrector_wedge512_{'fp32' if prec_tag == 'f32' else 'fp64'}.md")
     src = os.path.join(ROOT, "paper_2211_12867_gb300", "csrc", "k_stage.cu")
@@ -175,12 +177,25 @@ def roofline_traffic(prec_tag):
         text = open(path).read()
         h = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
         m = re.search(r"sha256\[:16\] = `([0-9a-f]{16})`", text)
-        t = re.search(r"traffic_bytes_per_launch = (\d+)", text)
+        t = re.search(key + r" = (\d+)", text)
         if not m or not t or m.group(1) != h:
             return None
         return float(t.group(1))
     except OSError:
         return None
+
+
+def roofline_traffic(prec_tag):
+    return profile_figure(prec_tag, "traffic_bytes_per_launch")
+
+
+def alu_peaks():
+    """measured FMA throughput of this GPU (TFLOP/s): FP64, FP32 (the better
+    of scalar and packed pairs)"""
+    from paper_2211_12867_gb300.icarus import alu_peak
+    return {"fp64_tflops": alu_peak(0) / 1e12, "fp32_tflops": max(alu_peak(1), alu_peak(2)) / 1e12,
+            "fp32_scalar_tflops": alu_peak(1) / 1e12, "how": "eight independent FMA chains per thread, "
+            "8 CTAs of 256 threads per SM, best of 5 (icarus_alu_peak)"}
 
 
 def _oracle_sample():
@@ -242,9 +257,11 @@ def run_reference(args):
     cb = {"value": value, "unit": "cell-updates/s", "cores": cores, "kind": "oracle", "sample": sample}
     line = {"metric": "cell-updates/s", "value": value, "unit": "cell-updates/s", "n_gpus": args.gpus,
             "steps": steps, "warmup": args.warmup,
-            "ms_per_step": 1e3 * int(np.prod(N_CELLS)) / value,   # a full 512x60x180 step at this rate
+            "ms_per_step": 1e3 * el / steps,                      # measured: one step of the sample
+            "ms_per_step_full_grid_extrapolated": 1e3 * int(np.prod(N_CELLS)) / value,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": WORKLOAD, "cells": int(np.prod(N_CELLS)), "sample": sample},
+            "config": {"workload": WORKLOAD, "cells": int(np.prod(N_CELLS)), "sample_cells": cells,
+                       "sample": sample},
             "impl": "reference", "cpu_baseline": cb,
             "e2e": {"value": value, "unit": "cell-updates/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
@@ -505,6 +522,7 @@ def main():
         best, best_ms, _ = tune(g, steps=3)
         tuned = {"tile": [best[0], best[1]], "r_segment": best[2], "ms": round(best_ms, 4)}
     cells = int(np.prod(N_CELLS))
+    peaks_alu = alu_peaks() if args.mode != "kernel" else None
     g.step(args.warmup, want_time=False)
     g.stream.synchronize()
     if args.mode == "kernel":
@@ -550,11 +568,34 @@ def main():
     corr_ms = per_kernel["stage_corrector"]["avg_ms"]
     achieved = BYTES_PER_CELL_CORRECTOR[prec_tag] * cells / (corr_ms / 1e3) / 1e9
     traffic = roofline_traffic(prec_tag)
-    roofline = {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s", "frac": achieved / hbm,
+    clocks = clk.summary()
+    hbm_roof = {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s", "frac": achieved / hbm,
                 "traffic": traffic, "kernel": "k_stage (corrector)", "peak_source": peak_kind,
                 "algorithmic_bytes_per_cell": BYTES_PER_CELL_CORRECTOR[prec_tag],
                 "step_frac": BYTES_PER_CELL_STEP[prec_tag] * cells / (ms / args.steps / 1e3) / 1e9 / hbm,
                 "profiled_ms_per_step": prof_step_ms, "kernels": per_kernel}
+    # instruction issue roof of the corrector: warp instructions of one
+    # launch (ncu, same source) over SMs x 4 schedulers x the SM clock
+    wi = profile_figure(prec_tag, "warp_inst_per_launch")
+    props = torch.cuda.get_device_properties(0)
+    mhz = clocks.get("sm_mhz") or 2070.0
+    issue_peak = props.multi_processor_count * 4 * mhz * 1e6
+    hbm_roof["issue"] = None if wi is None else {
+        "achieved_warp_inst_per_s": wi / (corr_ms / 1e3), "peak_warp_inst_per_s": issue_peak,
+        "frac": wi / (corr_ms / 1e3) / issue_peak, "warp_inst_per_cell": wi / cells,
+        "peak_note": "SMs x 4 schedulers x median SM clock of the timed region"}
+    if prec_tag == "f64":
+        # FP64 mode is bound by the FP64 pipe: executed FP64 flops of one
+        # corrector launch (ncu, same source) against the measured FMA peak
+        fl = profile_figure(prec_tag, "fp64_flop_per_launch")
+        peak64 = peaks_alu["fp64_tflops"]
+        ach = None if fl is None else fl / (corr_ms / 1e3) / 1e12
+        roofline = {"bound": "fp64", "achieved": ach, "peak": peak64, "unit": "TFLOP/s",
+                    "frac": None if ach is None else ach / peak64, "traffic": traffic,
+                    "kernel": "k_stage (corrector)", "peak_source": "measured (icarus_alu_peak, FP64 FMA)",
+                    "flop_per_cell": None if fl is None else fl / cells, "hbm": hbm_roof, "kernels": per_kernel}
+    else:
+        roofline = hbm_roof
 
     # ---- end to end through the public API, host buffers ----
     from paper_2211_12867_gb300.icarus import Icarus  # noqa: F401
@@ -592,8 +633,8 @@ def main():
                            "fp64_islands": {"p_over_e": isl[0], "beta": isl[1]} if prec_tag == "f32" else None,
                            "cells": cells, "l2": "state > L2 (no flush needed)", "parallelism": f"replicas{world}",
                            "tuned": tuned},
-                "roofline": roofline, "cpu_baseline": cb, "e2e": e2e, "gpu_launches": kps * args.steps,
-                "clocks": clk.summary(), "status_word": word, "floor_hits": floor_hits}
+                "roofline": roofline, "alu_peaks": peaks_alu, "cpu_baseline": cb, "e2e": e2e,
+                "gpu_launches": kps * args.steps, "clocks": clocks, "status_word": word, "floor_hits": floor_hits}
         print(json.dumps(line), flush=True)
     grp.close()
     return 0

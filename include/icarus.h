@@ -68,7 +68,14 @@ typedef enum {
 enum { ICARUS_FP64 = 0, ICARUS_FP32_MIXED = 1 };
 enum { ICARUS_SPHERICAL = 0, ICARUS_CARTESIAN = 1 };
 enum { ICARUS_BC_PERIODIC = 0, ICARUS_BC_OUTFLOW = 1, ICARUS_BC_REFLECT = 2, ICARUS_BC_INNER = 3 };
-enum { ICARUS_FLAG_PLAIN = 0, ICARUS_FLAG_LEARNED = 1, ICARUS_FLAG_BOTH = 2, ICARUS_FLAG_SHOCK = 3 };
+enum {
+  ICARUS_FLAG_PLAIN = 0,
+  ICARUS_FLAG_LEARNED = 1,
+  ICARUS_FLAG_BOTH = 2,
+  ICARUS_FLAG_SHOCK = 3,
+  ICARUS_FLAG_TRACER = 4,
+  ICARUS_FLAG_COMBINED = 5
+};
 
 /* Grid descriptor.
  *   n_cells      base-level cells (r, theta, phi); must be multiples of block.
@@ -89,7 +96,9 @@ enum { ICARUS_FLAG_PLAIN = 0, ICARUS_FLAG_LEARNED = 1, ICARUS_FLAG_BOTH = 2, ICA
  *                set on both sides; ICARUS_BC_INNER only at r low.
  *   max_blocks   capacity of the block pool (all members); 0 = base blocks.
  *   arena        caller-owned device memory, 256-byte aligned.
- *   stream       cudaStream_t (NULL = legacy default stream). */
+ *   stream       cudaStream_t (NULL = legacy default stream).
+ *   tracer       1: store and advect the CME density tracer rho X (Sect. 3.1;
+ *                see icarus_get_tracer), one more variable per cell; 0: none. */
 typedef struct {
   int n_cells[3];
   int block[3];
@@ -106,6 +115,7 @@ typedef struct {
   void *arena;
   size_t arena_bytes;
   void *stream;
+  int tracer;
 } icarus_grid_desc;
 
 /* Cone CME (Eqs. 1-4): injected while t_start <= t <= t_start + t_max and the
@@ -133,11 +143,20 @@ typedef struct {
  * off).  A block is flagged +1 if some interior cell counts, -1 (coarsen:
  * the criterion no longer holds) otherwise.  Evaluated in FP64 with
  * explicitly rounded operations.  ICARUS_ERR_ARG for div_thr < 0 or a half
- * width >= pi.  The last five fields are read in the shock mode only. */
+ * width >= pi.
+ * ICARUS_FLAG_TRACER (Sect. 3.1; needs a descriptor with tracer = 1): a cell
+ * counts where its CME tracer fraction X = (rho X) / rho exceeds x_thr (the
+ * paper refines where X is non-zero: x_thr = 0), inside the same windows
+ * (the paper applies none here: set the half widths to 0).
+ * ICARUS_FLAG_COMBINED (Sect. 3.3): a cell counts where X > x_thr or the
+ * velocity divergence is below -div_thr, inside the windows.  Both: +1 if
+ * some interior cell counts, -1 otherwise; ICARUS_ERR_STATE without tracer.
+ * The fields after mode are read in these three modes only. */
 typedef struct {
   double e_refine, e_coarsen, eps, dv;
   int mode;
   double div_thr, dlon_earth, dcolat_earth, dlon_cme;
+  double x_thr;
 } icarus_refine;
 
 /* Bytes of device arena that icarus_init_grid needs for this descriptor
@@ -245,6 +264,17 @@ icarus_status icarus_get_state(icarus_ctx *ctx, int member, double *host, size_t
  * ICARUS_ERR_ARG for a bad member, leaf or n.  Synchronises. */
 icarus_status icarus_get_padded(icarus_ctx *ctx, int member, int leaf, double *host, size_t n);
 
+/* The CME tracer rho X (Sect. 3.1) of a member's leaves, host FP64
+ * [leaf][i][j][k] over interior cells (n = leaves * cells per block), leaves
+ * in Morton order.  The tracer is the CME's mass fraction X stored as rho X;
+ * it enters with X = 1 through the inner-boundary cells the cone CME covers
+ * (X = 0 elsewhere) and is carried by each face's mass flux with X from the
+ * face's upwind cell, in both stages; it is prolonged and restricted like the
+ * other variables (not refluxed).  ICARUS_ERR_STATE if the descriptor has no
+ * tracer, ICARUS_ERR_ARG for a bad member or n.  Synchronise. */
+icarus_status icarus_get_tracer(icarus_ctx *ctx, int member, double *host, size_t n);
+icarus_status icarus_set_tracer(icarus_ctx *ctx, int member, const double *host, size_t n);
+
 /* member time (host write / read) */
 icarus_status icarus_set_time(icarus_ctx *ctx, int member, double t);
 
@@ -309,7 +339,7 @@ icarus_status icarus_set_tile(icarus_ctx *ctx, int tile_theta, int tile_phi, int
  * the context is poisoned.  0 disables the budget.  Default
  * ICARUS_DEFAULT_FLOOR_BUDGET.  Not stored in checkpoints.  ICARUS_ERR_ARG for
  * a negative or NaN fraction. */
-#define ICARUS_DEFAULT_FLOOR_BUDGET 0.05
+#define ICARUS_DEFAULT_FLOOR_BUDGET 0.1
 icarus_status icarus_set_floor_budget(icarus_ctx *ctx, double max_fraction);
 
 /* FP32 mode: the pressure of a cell is recomputed in FP64 (from the stored
@@ -365,6 +395,13 @@ icarus_status icarus_mlp_dataset_add(icarus_ctx *ctx, const float *x_host, const
  * loss_per_epoch (optional, epochs floats) receives the summed loss. */
 icarus_status icarus_mlp_train(icarus_ctx *ctx, int n_train, int epochs, int batch, double lr, uint64_t seed,
                                float *loss_per_epoch);
+
+/* Measured arithmetic peak of the current device on `stream` (cudaStream_t,
+ * NULL = legacy default): kind 0 FP64 FMA, 1 FP32 FMA, 2 FP32 FMA on packed
+ * pairs; *flops_per_s counts two flops per FMA.  The rooflines of the FP64
+ * and FP32 stage kernels are taken against these figures.  Synchronises;
+ * allocates nothing.  (A measurement helper; the paper has no counterpart.) */
+icarus_status icarus_alu_peak(int kind, void *stream, double *flops_per_s);
 
 /* Per-launch timing with CUDA events (enable = 1).  While enabled,
  * icarus_step launches the kernels directly instead of replaying the graph

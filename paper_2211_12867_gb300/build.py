@@ -18,7 +18,7 @@ BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libicarus.so")
 INCLUDE = os.path.join(os.path.dirname(HERE), "include")
 
-SOURCES = ["api.cu", "k_stage.cu", "k_ghost.cu", "k_amr.cu", "k_mlp.cu", "k_sums_static.cu"]
+SOURCES = ["api.cu", "k_stage.cu", "k_ghost.cu", "k_amr.cu", "k_mlp.cu", "k_sums_static.cu", "k_peak.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 # host code without floating-point contraction: the geometry tables come out
 # bit for bit the same on every host architecture

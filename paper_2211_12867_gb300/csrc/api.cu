@@ -89,6 +89,7 @@ icarus_status validate(const icarus_grid_desc *d) {
   if (d->max_level < 1 || d->max_level > MAXLEV) return ICARUS_ERR_ARG;
   if (d->n_members < 1 || d->n_members > 4096) return ICARUS_ERR_ARG;
   if (d->precision != ICARUS_FP64 && d->precision != ICARUS_FP32_MIXED) return ICARUS_ERR_ARG;
+  if (d->tracer != 0 && d->tracer != 1) return ICARUS_ERR_ARG;
   if (d->geometry != ICARUS_SPHERICAL && d->geometry != ICARUS_CARTESIAN) return ICARUS_ERR_ARG;
   for (int k = 0; k < 3; k++) {
     if (d->block[k] < 4 || d->block[k] % 2 || d->block[k] + 2 * NGH > 1024) return ICARUS_ERR_ARG;
@@ -122,9 +123,10 @@ Layout make_layout(const icarus_grid_desc *d) {
   L.tables = L.add(L.table_doubles * (8 + 4));
   L.blk = L.add(mb * sizeof(DevBlock));
   L.blk_alt = L.add(amr ? mb * sizeof(DevBlock) : 0);
-  L.U = L.add(mb * NVAR * pc * rs);
-  L.Us = L.add(mb * NVAR * pc * rs);
-  L.Ualt = L.add(amr ? mb * NVAR * pc * rs : 0);
+  const size_t nvs = NVAR + (d->tracer ? 1 : 0);   // variables stored per cell
+  L.U = L.add(mb * nvs * pc * rs);
+  L.Us = L.add(mb * nvs * pc * rs);
+  L.Ualt = L.add(amr ? mb * nvs * pc * rs : 0);
   const size_t fcells = 2 * ((size_t)d->block[1] * d->block[2] + (size_t)d->block[0] * d->block[2] +
                              (size_t)d->block[0] * d->block[1]);
   L.flux = L.add(amr ? mb * NVAR * fcells * rs : 0);
@@ -525,6 +527,7 @@ icarus_status upload_tree(icarus_ctx *c, DevBlock *blk_dst) {
 void fill_kp(icarus_ctx *c) {
   KParams &k = c->kp;
   const icarus_grid_desc &d = c->d;
+  k.nvs = NVAR + (d.tracer ? 1 : 0);
   for (int i = 0; i < 3; i++) {
     k.nb[i] = d.block[i];
     k.P[i] = d.block[i] + 2 * NGH;
@@ -737,8 +740,9 @@ void prof_mark(icarus_ctx *c, int kind, int end) {
 }
 void default_tiles(icarus_ctx *c) {
   const int n1 = c->d.block[1], n2 = c->d.block[2];
+  const int trc = c->d.tracer;
   if (c->tile_j && c->tile_k) {
-    c->occ = stage_max_ctas_per_sm(c->prec, c->tile_j, c->tile_k);
+    c->occ = stage_max_ctas_per_sm(c->prec, c->tile_j, c->tile_k, trc);
     return;
   }
   if (c->prec && n1 >= 12 && n2 >= 20) {
@@ -754,7 +758,11 @@ void default_tiles(icarus_ctx *c) {
     c->tile_j = 8;
     c->tile_k = 8;
   }
-  c->occ = stage_max_ctas_per_sm(c->prec, c->tile_j, c->tile_k);
+  if (!stage_tile_supported(c->prec, c->tile_j, c->tile_k, trc)) {
+    c->tile_j = 8;
+    c->tile_k = 8;
+  }
+  c->occ = stage_max_ctas_per_sm(c->prec, c->tile_j, c->tile_k, trc);
 }
 
 StageLaunch stage_cfg(icarus_ctx *c, int stage2) {
@@ -1190,7 +1198,7 @@ icarus_status icarus_set_member_max_level(icarus_ctx *c, int member, int L) {
 icarus_status icarus_set_tile(icarus_ctx *c, int tj, int tk, int seg) {
   if (!c) return ICARUS_ERR_ARG;
   if (tj || tk) {
-    if (!stage_tile_supported(c->prec, tj, tk)) return ICARUS_ERR_ARG;
+    if (!stage_tile_supported(c->prec, tj, tk, c->d.tracer)) return ICARUS_ERR_ARG;
     c->tile_j = tj;
     c->tile_k = tk;
     default_tiles(c);
@@ -1379,7 +1387,8 @@ icarus_status icarus_get_padded(icarus_ctx *c, int member, int leaf, double *hos
   if (leaf < 0 || leaf >= nl || n != (size_t)NVAR * c->kp.pcells) return ICARUS_ERR_ARG;
   const size_t slot = (size_t)c->mem_off[member] + leaf;
   std::vector<unsigned char> raw(n * c->rsize);
-  CK(cudaMemcpyAsync(raw.data(), static_cast<const char *>(c->U) + slot * raw.size(), raw.size(),
+  const size_t stride = (size_t)c->kp.nvs * c->kp.pcells * c->rsize;   // bytes per slot
+  CK(cudaMemcpyAsync(raw.data(), static_cast<const char *>(c->U) + slot * stride, raw.size(),
                      cudaMemcpyDeviceToHost, c->stream));
   CK(cudaStreamSynchronize(c->stream));
   if (c->prec) {
@@ -1389,6 +1398,74 @@ icarus_status icarus_get_padded(icarus_ctx *c, int member, int leaf, double *hos
     memcpy(host, raw.data(), raw.size());
   }
   return ICARUS_OK;
+}
+
+}  // extern "C"
+
+namespace {
+
+// the tracer plane (padded) of every leaf of a member into / out of host
+// memory: one strided copy
+icarus_status tracer_planes(icarus_ctx *c, int member, std::vector<unsigned char> &raw, bool to_host) {
+  const size_t nl = c->mem[member].leaves.size();
+  const size_t plane = (size_t)c->kp.pcells * c->rsize, stride = (size_t)c->kp.nvs * plane;
+  char *base = static_cast<char *>(c->U) + (size_t)c->mem_off[member] * stride + (size_t)TRV * plane;
+  if (to_host) {
+    raw.resize(nl * plane);
+    CK(cudaMemcpy2DAsync(raw.data(), plane, base, stride, plane, nl, cudaMemcpyDeviceToHost, c->stream));
+  } else {
+    CK(cudaMemcpy2DAsync(base, stride, raw.data(), plane, plane, nl, cudaMemcpyHostToDevice, c->stream));
+  }
+  CK(cudaStreamSynchronize(c->stream));
+  return ICARUS_OK;
+}
+
+template <typename F>
+void for_interior(const icarus_ctx *c, F f) {
+  const int *nb = c->d.block;
+  const int P1 = nb[1] + 2 * NGH, P2 = nb[2] + 2 * NGH;
+  size_t q = 0;
+  for (int i = 0; i < nb[0]; i++)
+    for (int j = 0; j < nb[1]; j++)
+      for (int k = 0; k < nb[2]; k++, q++) f(q, ((size_t)(i + NGH) * P1 + j + NGH) * P2 + k + NGH);
+}
+
+}  // namespace
+
+extern "C" {
+
+icarus_status icarus_get_tracer(icarus_ctx *c, int member, double *host, size_t n) {
+  if (!member_ok(c, member) || !host) return ICARUS_ERR_ARG;
+  if (!c->d.tracer) return ICARUS_ERR_STATE;
+  const size_t nl = c->mem[member].leaves.size(), ic = (size_t)c->kp.icells, pc = (size_t)c->kp.pcells;
+  if (n != nl * ic) return ICARUS_ERR_ARG;
+  std::vector<unsigned char> raw;
+  icarus_status st = tracer_planes(c, member, raw, true);
+  if (st != ICARUS_OK) return st;
+  for (size_t b = 0; b < nl; b++)
+    for_interior(c, [&](size_t q, size_t pidx) {
+      host[b * ic + q] = c->prec ? (double)reinterpret_cast<const float *>(raw.data())[b * pc + pidx]
+                                 : reinterpret_cast<const double *>(raw.data())[b * pc + pidx];
+    });
+  return ICARUS_OK;
+}
+
+icarus_status icarus_set_tracer(icarus_ctx *c, int member, const double *host, size_t n) {
+  if (!member_ok(c, member) || !host) return ICARUS_ERR_ARG;
+  if (!c->d.tracer) return ICARUS_ERR_STATE;
+  if (c->poisoned) return ICARUS_ERR_STATE;
+  const size_t nl = c->mem[member].leaves.size(), ic = (size_t)c->kp.icells, pc = (size_t)c->kp.pcells;
+  if (n != nl * ic) return ICARUS_ERR_ARG;
+  c->ghosts_fresh = false;
+  std::vector<unsigned char> raw;
+  icarus_status st = tracer_planes(c, member, raw, true);   // keep the ghost layers
+  if (st != ICARUS_OK) return st;
+  for (size_t b = 0; b < nl; b++)
+    for_interior(c, [&](size_t q, size_t pidx) {
+      if (c->prec) reinterpret_cast<float *>(raw.data())[b * pc + pidx] = (float)host[b * ic + q];
+      else reinterpret_cast<double *>(raw.data())[b * pc + pidx] = host[b * ic + q];
+    });
+  return tracer_planes(c, member, raw, false);
 }
 
 icarus_status icarus_get_dt(icarus_ctx *c, double *dt) {
@@ -1449,15 +1526,21 @@ icarus_status icarus_probe(icarus_ctx *c, int member, int n_pts, const double *r
 
 icarus_status icarus_flag_refine(icarus_ctx *c, const icarus_refine *crit, int8_t *flags_out) {
   if (!c || !crit) return ICARUS_ERR_ARG;
-  if (crit->mode < ICARUS_FLAG_PLAIN || crit->mode > ICARUS_FLAG_SHOCK) return ICARUS_ERR_ARG;
+  if (crit->mode < ICARUS_FLAG_PLAIN || crit->mode > ICARUS_FLAG_COMBINED) return ICARUS_ERR_ARG;
+  if ((crit->mode == ICARUS_FLAG_TRACER || crit->mode == ICARUS_FLAG_COMBINED) && !c->d.tracer)
+    return ICARUS_ERR_STATE;
   if (c->poisoned) return ICARUS_ERR_STATE;
   if (!c->ghosts_fresh) {
     enqueue_ghost(c, c->U, 0.0);
     c->ghosts_fresh = true;
   }
-  if (crit->mode == ICARUS_FLAG_SHOCK) {
-    const double w[4] = {crit->div_thr, crit->dlon_earth, crit->dcolat_earth, crit->dlon_cme};
-    if (!(w[0] >= 0.0) || !(w[1] < M_PI) || !(w[2] < M_PI) || !(w[3] < M_PI)) return ICARUS_ERR_ARG;
+  if (crit->mode >= ICARUS_FLAG_SHOCK) {
+    // shock (0), tracer (1) or combined (2) criterion
+    const int which = crit->mode - ICARUS_FLAG_SHOCK;
+    const double w[6] = {crit->div_thr, crit->dlon_earth, crit->dcolat_earth, crit->dlon_cme, crit->x_thr,
+                         (double)which};
+    if (!(w[0] >= 0.0) || !(w[1] < M_PI) || !(w[2] < M_PI) || !(w[3] < M_PI) || !(w[4] >= 0.0))
+      return ICARUS_ERR_ARG;
     shock_estimator_launch(c->kp, c->U, c->prec, 0, c->nleaves, w, c->flags, c->stream);
   } else {
     estimator_launch(c->kp, c->U, c->prec, 0, c->nleaves, crit->e_refine, crit->e_coarsen, crit->eps, crit->dv,
@@ -1859,6 +1942,7 @@ std::vector<double> ck_fingerprint(const icarus_grid_desc &d) {
   f.push_back(d.n_members);
   for (int k = 0; k < 3; k++) f.push_back(d.bc_lo[k]);
   for (int k = 0; k < 3; k++) f.push_back(d.bc_hi[k]);
+  f.push_back(d.tracer);
   return f;
 }
 
@@ -1876,7 +1960,7 @@ struct CkFile {
   }
 };
 
-size_t slot_bytes(const icarus_ctx *c) { return (size_t)NVAR * c->kp.pcells * c->rsize; }
+size_t slot_bytes(const icarus_ctx *c) { return (size_t)c->kp.nvs * c->kp.pcells * c->rsize; }
 
 }  // namespace
 

@@ -4,6 +4,7 @@
 #include <stdint.h>
 
 #define NVAR 8
+#define TRV 8          // index of the CME tracer rho X in a slot (when stored)
 #define NGH 2
 #define MAXLEV 8
 
@@ -81,6 +82,8 @@ struct DevEarth {
 // everything a kernel needs to know about the grid (passed by value)
 struct KParams {
   int nb[3], P[3];
+  int nvs;                     // variables stored per cell: NVAR, or NVAR + 1 with the CME tracer rho X
+  int pad_nvs;
   int pcells, icells;
   int nbase[3];
   int n_members;
@@ -127,9 +130,10 @@ int stage_launch(const KParams &kp, const StageLaunch &sl, int precision, cudaSt
 // longest radial segment a stage work item marches (its geometry is staged
 // in shared memory)
 constexpr int STAGE_SEG_MAX = 64;
-size_t stage_smem_bytes(int precision, int tj, int tk);
-int stage_tile_supported(int precision, int tj, int tk);
-int stage_max_ctas_per_sm(int precision, int tj, int tk);
+// tracer: the CME tracer is stored and advected (one more shared ring)
+size_t stage_smem_bytes(int precision, int tj, int tk, int tracer);
+int stage_tile_supported(int precision, int tj, int tk, int tracer);
+int stage_max_ctas_per_sm(int precision, int tj, int tk, int tracer);
 
 // ghost fill
 void ghost_neighbour_launch(const KParams &kp, void *U, int precision, const int *list, int nlist,
@@ -149,7 +153,8 @@ void unpack_state_launch(const KParams &kp, void *U, int precision, int slot0, i
                          int is_prim, cudaStream_t s);
 void estimator_launch(const KParams &kp, const void *U, int precision, int slot0, int nslots, double e_ref,
                       double e_crs, double eps, double dv, signed char *flags, cudaStream_t s);
-// shock criterion: crit = {div_thr, dlon_earth, dcolat_earth, dlon_cme}
+// shock / tracer / combined criterion: crit = {div_thr, dlon_earth,
+// dcolat_earth, dlon_cme, x_thr, which (0 shock, 1 tracer, 2 combined)}
 void shock_estimator_launch(const KParams &kp, const void *U, int precision, int slot0, int nslots,
                             const double *crit, signed char *flags, cudaStream_t s);
 struct MoveOp {       // one new leaf of a regrid

@@ -14,7 +14,7 @@ namespace {
 
 template <typename real>
 __device__ __forceinline__ size_t cidx(const KParams &kp, int slot, int v, int p0, int p1, int p2) {
-  return ((((size_t)slot * NVAR + v) * kp.P[0] + p0) * kp.P[1] + p1) * kp.P[2] + p2;
+  return ((((size_t)slot * kp.nvs + v) * kp.P[0] + p0) * kp.P[1] + p1) * kp.P[2] + p2;
 }
 
 template <typename real>
@@ -147,9 +147,12 @@ __device__ __forceinline__ double vel(const KParams &kp, const real *U, int slot
   return __ddiv_rn((double)U[cidx<real>(kp, slot, v, p0, p1, p2)], (double)U[cidx<real>(kp, slot, 0, p0, p1, p2)]);
 }
 
+// which: 0 shock (div v < -div_thr), 1 tracer (X > x_thr), 2 combined
+// (either), all inside the windows.  The tracer fraction X = (rho X) / rho is
+// one correctly rounded division of the stored values.
 template <typename real>
 __global__ void k_shock_estimator(const KParams kp, const real *U, int slot0, double div_thr, double w_le,
-                                  double w_ce, double w_lc, signed char *flags) {
+                                  double w_ce, double w_lc, double x_thr, int which, signed char *flags) {
   const int slot = slot0 + blockIdx.x;
   const DevBlock B = kp.blk[slot];
   const LevelGeo<double> &G = kp.geo->d[B.level];
@@ -169,6 +172,11 @@ __global__ void k_shock_estimator(const KParams kp, const real *U, int slot0, do
     if (w_lc > 0.0) in = in && C.active && fabs(wrap_pi(__dsub_rn(ph, C.lon))) <= w_lc;
     if (!in) continue;
     const int p0 = i + NGH, p1 = j + NGH, p2 = k + NGH;
+    if (which >= 1 && vel(kp, U, slot, TRV, p0, p1, p2) > x_thr) {
+      refine = 1;
+      continue;
+    }
+    if (which == 1) continue;
     const double vrm = vel(kp, U, slot, 1, p0 - 1, p1, p2), vrp = vel(kp, U, slot, 1, p0 + 1, p1, p2);
     const double vtm = vel(kp, U, slot, 2, p0, p1 - 1, p2), vtp = vel(kp, U, slot, 2, p0, p1 + 1, p2);
     const double vpm = vel(kp, U, slot, 3, p0, p1, p2 - 1), vpp = vel(kp, U, slot, 3, p0, p1, p2 + 1);
@@ -199,12 +207,14 @@ template <typename real>
 __device__ void prolong_child(const KParams &kp, const real *U, int cs, const int *Ic, int ch, real *out) {
   const DevBlock C = kp.blk[cs];
   const int Lc = C.level;
+  const int nv = kp.nvs;   // the MHD variables and, when stored, the CME tracer
   int pc[3];
 #pragma unroll
   for (int d = 0; d < 3; d++) pc[d] = Ic[d] - C.ix[d] * kp.nb[d] + NGH;
-  real up[NVAR], s[3][NVAR];
+  real up[NVAR + 1], s[3][NVAR + 1];
 #pragma unroll
-  for (int v = 0; v < NVAR; v++) {
+  for (int v = 0; v < NVAR + 1; v++) {
+    if (v >= nv) break;
     up[v] = U[cidx<real>(kp, cs, v, pc[0], pc[1], pc[2])];
     s[0][v] = mc_slope<real>(U[cidx<real>(kp, cs, v, pc[0] - 1, pc[1], pc[2])], up[v],
                              U[cidx<real>(kp, cs, v, pc[0] + 1, pc[1], pc[2])]);
@@ -219,17 +229,20 @@ __device__ void prolong_child(const KParams &kp, const real *U, int cs, const in
   bool ok = true;
   for (int c = 0; c < 8; c++) {
     const real a = d0[2 * Ic[0] + ((c >> 2) & 1)], b = d1[2 * Ic[1] + ((c >> 1) & 1)], e = d2[2 * Ic[2] + (c & 1)];
-    real u[NVAR];
+    real u[NVAR + 1];
 #pragma unroll
-    for (int v = 0; v < NVAR; v++) u[v] = ((up[v] + s[0][v] * a) + s[1][v] * b) + s[2][v] * e;
+    for (int v = 0; v < NVAR + 1; v++)
+      if (v < nv) u[v] = ((up[v] + s[0][v] * a) + s[1][v] * b) + s[2][v] * e;
     if (!(u[0] > real(0)) || !(pressure_of<real>(u, gamma, Isl{(float)kp.isl_pe, (float)kp.isl_beta}) > real(0))) ok = false;
     if (c == ch)
 #pragma unroll
-      for (int v = 0; v < NVAR; v++) out[v] = u[v];
+      for (int v = 0; v < NVAR + 1; v++)
+        if (v < nv) out[v] = u[v];
   }
   if (!ok)
 #pragma unroll
-    for (int v = 0; v < NVAR; v++) out[v] = up[v];
+    for (int v = 0; v < NVAR + 1; v++)
+      if (v < nv) out[v] = up[v];
 }
 
 template <typename real>
@@ -240,10 +253,12 @@ __global__ void k_regrid_move(const KParams kpo, const real *Uold, real *Unew, c
   if (c >= kpo.icells) return;
   const int k = c % kpo.nb[2], j = (c / kpo.nb[2]) % kpo.nb[1], i = c / (kpo.nb[2] * kpo.nb[1]);
   const DevBlock N = nblk[op.dst];
-  real val[NVAR];
+  real val[NVAR + 1];
+  const int nv = kpo.nvs;
   if (op.kind == 0) {
 #pragma unroll
-    for (int v = 0; v < NVAR; v++) val[v] = Uold[cidx<real>(kpo, op.src[0], v, i + NGH, j + NGH, k + NGH)];
+    for (int v = 0; v < NVAR + 1; v++)
+      if (v < nv) val[v] = Uold[cidx<real>(kpo, op.src[0], v, i + NGH, j + NGH, k + NGH)];
   } else if (op.kind == 1) {
     const int F[3] = {N.ix[0] * kpo.nb[0] + i, N.ix[1] * kpo.nb[1] + j, N.ix[2] * kpo.nb[2] + k};
     const int Ic[3] = {F[0] >> 1, F[1] >> 1, F[2] >> 1};
@@ -251,9 +266,9 @@ __global__ void k_regrid_move(const KParams kpo, const real *Uold, real *Unew, c
   } else {
     const LevelGeo<real> &FG = GeoSel<real>::get(kpo.geo, N.level + 1);
     const int G[3] = {N.ix[0] * kpo.nb[0] + i, N.ix[1] * kpo.nb[1] + j, N.ix[2] * kpo.nb[2] + k};
-    real sum[NVAR];
+    real sum[NVAR + 1];
 #pragma unroll
-    for (int v = 0; v < NVAR; v++) sum[v] = real(0);
+    for (int v = 0; v < NVAR + 1; v++) sum[v] = real(0);
     real vs = real(0);
     for (int ch = 0; ch < 8; ch++) {
       const int f[3] = {2 * G[0] + ((ch >> 2) & 1), 2 * G[1] + ((ch >> 1) & 1), 2 * G[2] + (ch & 1)};
@@ -266,14 +281,16 @@ __global__ void k_regrid_move(const KParams kpo, const real *Uold, real *Unew, c
       const int q2 = f[2] - (2 * N.ix[2] + cb[2]) * kpo.nb[2] + NGH;
       const real V = FG.dr3[f[0] + NGH] * FG.dcos[f[1] + NGH] * FG.dphi;
 #pragma unroll
-      for (int v = 0; v < NVAR; v++) sum[v] += V * Uold[cidx<real>(kpo, os, v, q0, q1, q2)];
+      for (int v = 0; v < NVAR + 1; v++)
+        if (v < nv) sum[v] += V * Uold[cidx<real>(kpo, os, v, q0, q1, q2)];
       vs += V;
     }
 #pragma unroll
-    for (int v = 0; v < NVAR; v++) val[v] = sum[v] / vs;
+    for (int v = 0; v < NVAR + 1; v++) val[v] = sum[v] / vs;
   }
 #pragma unroll
-  for (int v = 0; v < NVAR; v++) Unew[cidx<real>(kpo, op.dst, v, i + NGH, j + NGH, k + NGH)] = val[v];
+  for (int v = 0; v < NVAR + 1; v++)
+    if (v < nv) Unew[cidx<real>(kpo, op.dst, v, i + NGH, j + NGH, k + NGH)] = val[v];
 }
 
 // ---- probe ----
@@ -443,12 +460,13 @@ void estimator_launch(const KParams &kp, const void *U, int precision, int slot0
 void shock_estimator_launch(const KParams &kp, const void *U, int precision, int slot0, int nslots,
                             const double *crit, signed char *flags, cudaStream_t s) {
   if (nslots <= 0) return;
+  const int which = (int)crit[5];
   if (precision)
     k_shock_estimator<float><<<nslots, 256, 0, s>>>(kp, (const float *)U, slot0, crit[0], crit[1], crit[2], crit[3],
-                                                     flags);
+                                                     crit[4], which, flags);
   else
     k_shock_estimator<double><<<nslots, 256, 0, s>>>(kp, (const double *)U, slot0, crit[0], crit[1], crit[2],
-                                                      crit[3], flags);
+                                                      crit[3], crit[4], which, flags);
 }
 
 void regrid_move_launch2(const KParams &kp_old, const void *Uold, void *Unew, const DevBlock *nblk, int precision,

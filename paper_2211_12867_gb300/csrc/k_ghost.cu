@@ -45,20 +45,28 @@ __device__ __forceinline__ int lookup(const KParams &kp, int member, int L, cons
 
 template <typename real>
 __device__ __forceinline__ size_t cell_index(const KParams &kp, int slot, int v, int p0, int p1, int p2) {
-  return ((((size_t)slot * NVAR + v) * kp.P[0] + p0) * kp.P[1] + p1) * kp.P[2] + p2;
+  return ((((size_t)slot * kp.nvs + v) * kp.P[0] + p0) * kp.P[1] + p1) * kp.P[2] + p2;
 }
 
-// prolonged value of child `ch` of coarse cell Ic (global at level Lc) held
-// by leaf slot cs; positivity is checked on all 8 children.
+// Conservative prolongation of coarse cell Ic (global at level Lc, held by
+// leaf slot cs) into the 2 x 2 x 2 ghost cells of leaf `slot` starting at
+// padded index p: child (i, j, k) = parent + MC slopes x offsets; if any
+// child's density or pressure is not positive all eight take the parent
+// value.  A first pass checks the eight children, a second writes them
+// (no per-child arrays held in registers).
 template <typename real>
-__device__ void prolong_value(const KParams &kp, const real *U, int cs, int Lc, const int *Ic, int ch, real *out) {
+__device__ void prolong_into(const KParams &kp, real *U, int cs, int Lc, const int *Ic, int slot, const int *p) {
   const DevBlock C = kp.blk[cs];
   int pc[3];
 #pragma unroll
   for (int d = 0; d < 3; d++) pc[d] = Ic[d] - C.ix[d] * kp.nb[d] + NGH;
-  real up[NVAR], s[3][NVAR];
+  // the MHD variables and, when stored, the CME tracer (same slopes and
+  // offsets; the positivity decision is the MHD variables')
+  const int nv = kp.nvs;
+  real up[NVAR + 1], s[3][NVAR + 1];
 #pragma unroll
-  for (int v = 0; v < NVAR; v++) {
+  for (int v = 0; v < NVAR + 1; v++) {
+    if (v >= nv) break;
     up[v] = U[cell_index<real>(kp, cs, v, pc[0], pc[1], pc[2])];
     s[0][v] = mc_slope<real>(U[cell_index<real>(kp, cs, v, pc[0] - 1, pc[1], pc[2])], up[v],
                              U[cell_index<real>(kp, cs, v, pc[0] + 1, pc[1], pc[2])]);
@@ -77,14 +85,15 @@ __device__ void prolong_value(const KParams &kp, const real *U, int cs, int Lc, 
 #pragma unroll
     for (int v = 0; v < NVAR; v++) u[v] = ((up[v] + s[0][v] * a) + s[1][v] * b) + s[2][v] * e;
     if (!(u[0] > real(0)) || !(pressure_of<real>(u, gamma, Isl{(float)kp.isl_pe, (float)kp.isl_beta}) > real(0))) ok = false;
-    if (c == ch) {
-#pragma unroll
-      for (int v = 0; v < NVAR; v++) out[v] = u[v];
-    }
   }
-  if (!ok) {
+  for (int c = 0; c < 8; c++) {
+    const real a = d0[2 * Ic[0] + ((c >> 2) & 1)], b = d1[2 * Ic[1] + ((c >> 1) & 1)], e = d2[2 * Ic[2] + (c & 1)];
+    const int q0 = p[0] + ((c >> 2) & 1), q1 = p[1] + ((c >> 1) & 1), q2 = p[2] + (c & 1);
 #pragma unroll
-    for (int v = 0; v < NVAR; v++) out[v] = up[v];
+    for (int v = 0; v < NVAR + 1; v++) {
+      if (v >= nv) break;
+      U[cell_index<real>(kp, slot, v, q0, q1, q2)] = ok ? ((up[v] + s[0][v] * a) + s[1][v] * b) + s[2][v] * e : up[v];
+    }
   }
 }
 
@@ -102,9 +111,10 @@ template <typename real>
 __device__ bool restrict_in_block(const KParams &kp, const real *U, int member, int L, const int *b, const int *q,
                                   const int *G, real *out) {
   const LevelGeo<real> &F = GeoSel<real>::get(kp.geo, L + 1);
-  real sum[NVAR];
+  const int nv = kp.nvs;
+  real sum[NVAR + 1];
 #pragma unroll
-  for (int v = 0; v < NVAR; v++) sum[v] = real(0);
+  for (int v = 0; v < NVAR + 1; v++) sum[v] = real(0);
   real vs = real(0);
   for (int c = 0; c < 8; c++) {
     const int cb[3] = {(c >> 2) & 1, (c >> 1) & 1, c & 1};
@@ -121,11 +131,12 @@ __device__ bool restrict_in_block(const KParams &kp, const real *U, int member, 
     const int f0 = 2 * G[0] + cb[0], f1 = 2 * G[1] + cb[1];
     const real V = F.dr3[f0 + NGH] * F.dcos[f1 + NGH] * F.dphi;
 #pragma unroll
-    for (int v = 0; v < NVAR; v++) sum[v] += V * U[cell_index<real>(kp, fs, v, fq[0], fq[1], fq[2])];
+    for (int v = 0; v < NVAR + 1; v++)
+      if (v < nv) sum[v] += V * U[cell_index<real>(kp, fs, v, fq[0], fq[1], fq[2])];
     vs += V;
   }
 #pragma unroll
-  for (int v = 0; v < NVAR; v++) out[v] = sum[v] / vs;
+  for (int v = 0; v < NVAR + 1; v++) out[v] = sum[v] / vs;
   return true;
 }
 
@@ -158,12 +169,18 @@ __global__ void __launch_bounds__(256, sizeof(real) == 4 ? 4 : 2) k_ghost_neighb
     q[d] = p[d] - side * nb;          // padded index inside block b
     G[d] = bd * nb + q[d] - NGH;      // global cell at level L
   }
-  real val[NVAR];
+  real val[NVAR + 1];
+  const int nv = kp.nvs;
   const int o = lookup_block(kp, member, L, b);
   if (o >= 0) {
 #pragma unroll
-    for (int v = 0; v < NVAR; v++) val[v] = U[cell_index<real>(kp, o, v, q[0], q[1], q[2])];
+    for (int v = 0; v < NVAR + 1; v++)
+      if (v < nv) val[v] = U[cell_index<real>(kp, o, v, q[0], q[1], q[2])];
   } else if (o == -1) {
+    // A coarse cell covers a 2 x 2 x 2 group of ghost cells (blocks start at
+    // even global indices and there are two ghost layers): the group's
+    // first cell computes the eight children once and writes all of them.
+    if ((p[0] | p[1] | p[2]) & 1) return;
     int cb[3], Ic[3];
 #pragma unroll
     for (int d = 0; d < 3; d++) {
@@ -175,7 +192,8 @@ __global__ void __launch_bounds__(256, sizeof(real) == 4 ? 4 : 2) k_ghost_neighb
       atomicOr(kp.status, ST_NAN);
       return;
     }
-    prolong_value<real>(kp, U, cs, L - 1, Ic, ((G[0] & 1) << 2) | ((G[1] & 1) << 1) | (G[2] & 1), val);
+    prolong_into<real>(kp, U, cs, L - 1, Ic, slot, p);
+    return;
   } else {
     if (!restrict_in_block<real>(kp, U, member, L, b, q, G, val)) {
       atomicOr(kp.status, ST_NAN);
@@ -183,11 +201,14 @@ __global__ void __launch_bounds__(256, sizeof(real) == 4 ? 4 : 2) k_ghost_neighb
     }
   }
 #pragma unroll
-  for (int v = 0; v < NVAR; v++) U[cell_index<real>(kp, slot, v, p[0], p[1], p[2])] = val[v];
+  for (int v = 0; v < NVAR + 1; v++)
+    if (v < nv) U[cell_index<real>(kp, slot, v, p[0], p[1], p[2])] = val[v];
 }
 
-// inner boundary state (FP64): map of the containing base cell, cone CME overlay
+// inner boundary state (FP64): map of the containing base cell, cone CME
+// overlay; u[TRV] = rho X with the CME tracer X = 1 in the CME plasma, else 0
 __device__ void inner_state(const KParams &kp, int member, int L, int J, int K, double t, double *u) {
+  double X = 0.0;
   const int n1 = kp.n_base_cells[1], n2 = kp.n_base_cells[2];
   const int jb = J >> (L - 1), kb = K >> (L - 1);
   const double *m = kp.bmap + (size_t)member * NVAR * n1 * n2;
@@ -215,11 +236,13 @@ __device__ void inner_state(const KParams &kp, int member, int L, int J, int K, 
           w[3] = -kp.omega * R * sin(th);
           w[4] = c.p;
           w[5] = w[6] = w[7] = 0.0;
+          X = 1.0;
         }
       }
     }
   }
   prim2cons<double>(w, u, 1.0 / (kp.gamma - 1.0));
+  u[TRV] = w[0] * X;
 }
 
 // physical boundary of direction `dir`; sides[n] = (slot, side)
@@ -250,15 +273,17 @@ __global__ void k_ghost_physical(const KParams kp, real *U, const int2 *sides, i
     const int K = wrap_dim(kp, L, 2, B.ix[2] * kp.nb[2] + q[2] - NGH, in2);
     if (!in1 || !in2) return;
     const double t = kp.t[B.member] + tfac * kp.dt_used[B.member];
-    double u[NVAR];
+    double u[NVAR + 1];
     inner_state(kp, B.member, L, J, K, t, u);
 #pragma unroll
-    for (int v = 0; v < NVAR; v++) U[cell_index<real>(kp, slot, v, q[0], q[1], q[2])] = (real)u[v];
+    for (int v = 0; v < NVAR + 1; v++)
+      if (v < kp.nvs) U[cell_index<real>(kp, slot, v, q[0], q[1], q[2])] = (real)u[v];
     return;
   }
   s[dir] = bc == 2 ? pm : pn;
 #pragma unroll
-  for (int v = 0; v < NVAR; v++) {
+  for (int v = 0; v < NVAR + 1; v++) {
+    if (v >= kp.nvs) break;
     real x = U[cell_index<real>(kp, slot, v, s[0], s[1], s[2])];
     if (bc == 2 && (v == 1 + dir || v == 5 + dir)) x = -x;
     U[cell_index<real>(kp, slot, v, q[0], q[1], q[2])] = x;

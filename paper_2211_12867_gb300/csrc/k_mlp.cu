@@ -42,7 +42,7 @@ __global__ void k_features(const KParams kp, const real *U, int slot0, float *ou
   const int s0 = n0 / 4, s1 = n1 / 4, s2 = n2 / 4;
   const double gm1 = kp.gamma - 1.0;
   auto cell = [&](int v, int i, int j, int k) -> double {
-    return (double)U[((((size_t)slot * NVAR + v) * kp.P[0] + i) * kp.P[1] + j) * kp.P[2] + k];
+    return (double)U[((((size_t)slot * kp.nvs + v) * kp.P[0] + i) * kp.P[1] + j) * kp.P[2] + k];
   };
   auto prims = [&](int i, int j, int k, double *w) {  // rho, v_r, p
     const double r = cell(0, i, j, k), m1 = cell(1, i, j, k), m2 = cell(2, i, j, k), m3 = cell(3, i, j, k);

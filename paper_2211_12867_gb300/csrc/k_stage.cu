@@ -32,10 +32,12 @@ namespace {
 
 template <typename real>
 struct StageSmem {
-  static constexpr size_t bytes(int tj, int tk) {
+  // tracer: a 5-plane ring of the CME tracer fraction X follows the rest
+  static constexpr size_t bytes(int tj, int tk, bool tracer = false) {
     return sizeof(real) * (size_t)(5 * NVAR * (tj + 4) * (tk + 4) + 2 * NVAR * (tj + 1) * tk +
                                    2 * NVAR * tj * (tk + 1) + 4 * (tj + 2) * (tk + 2) +
-                                   NVAR * ((tj * tk + 31) / 32 * 32) + geo(tj, tk));
+                                   NVAR * ((tj * tk + 31) / 32 * 32) + geo(tj, tk) +
+                                   (tracer ? 5 * (tj + 4) * (tk + 4) : 0));
   }
   // geometry of one work item: 4 plane arrays and the faces in r, 5 row
   // arrays and the faces in theta, the phi centres
@@ -137,12 +139,14 @@ __global__ void __launch_bounds__(stage_threads(TJ, TK), stage_min_ctas(sizeof(r
   real *s_tc = s_r2f + NRP + 1, *s_st = s_tc + NJ, *s_ct = s_st + NJ, *s_dcos = s_ct + NJ, *s_dth = s_dcos + NJ;
   real *s_sinf = s_dth + NJ;                                  // TJ + 5 faces
   real *s_pc = s_sinf + NJ + 1;                               // TK + 4
+  real *xring = s_pc + TK + 4;                                // tracer X, 5 planes (if stored)
+  const bool trc = kp.nvs > NVAR;
 
   const int tid = threadIdx.x, jl = tid / TK, kl = tid % TK;
   const real gamma = (real)kp.gamma, pfl = (real)kp.p_floor, rfl = (real)kp.rho_floor;
   const int nb0 = kp.nb[0], nb1 = kp.nb[1], nb2 = kp.nb[2];
   const int P1 = kp.P[1], P2 = kp.P[2];
-  const size_t plane = (size_t)P1 * P2, vstride = (size_t)kp.P[0] * plane, bstride = NVAR * vstride;
+  const size_t plane = (size_t)P1 * P2, vstride = (size_t)kp.P[0] * plane, bstride = kp.nvs * vstride;
   const int per_block = sl.tiles_j * sl.tiles_k * sl.segs;
   const int nwork = sl.nlist * per_block;
   const bool spherical = kp.geometry == 0;
@@ -192,6 +196,7 @@ __global__ void __launch_bounds__(stage_threads(TJ, TK), stage_min_ctas(sizeof(r
     // thread indices, which own no second div B position.
     constexpr int NU = RP / 2;
     auto slotp = [&](int p) -> real * { return ring + ((p + 5) % 5) * NVAR * RP; };
+    auto xslot = [&](int p) -> real * { return xring + ((p + 5) % 5) * RP; };
     auto issue_plane = [&](int p) {
       real *dst = slotp(p);
       const real *src = Uin + (size_t)(p + NGH) * plane;
@@ -204,6 +209,7 @@ __global__ void __launch_bounds__(stage_threads(TJ, TK), stage_min_ctas(sizeof(r
 #pragma unroll
             for (int v = 0; v < NVAR; v++)
               cp_async<sizeof(real)>(&el<real, RP>(dst, v, q), src + v * vstride + (size_t)pj * P2 + pk);
+            if (trc) cp_async<sizeof(real)>(xslot(p) + q, src + TRV * vstride + (size_t)pj * P2 + pk);
           }
         }
       }
@@ -220,6 +226,7 @@ __global__ void __launch_bounds__(stage_threads(TJ, TK), stage_min_ctas(sizeof(r
             ld8<real, RP>(pl, q, uu);
             cons2prim<real>(uu, wv, gamma, pfl, isl);
             st8<real, RP>(pl, q, wv);
+            if (trc) xslot(p)[q] *= RT<real>::rcp_(uu[0]);   // rho X -> X
           }
         }
       }
@@ -328,11 +335,13 @@ __global__ void __launch_bounds__(stage_threads(TJ, TK), stage_min_ctas(sizeof(r
       divb_plane(ib);
     }
     real Flo[NVAR], sc[NVAR];
+    real xprev = real(0);   // tracer X of this column at the previous plane
     if (valid) {
       real s0[NVAR];
       rslope(ib - 1, s0);
       rslope(ib, sc);
       rflux(ib, s0, sc, Flo);
+      if (trc) xprev = xslot(ib - 1)[(jl + 2) * RK + kl + 2];
     }
     __syncthreads();   // plane ib-2 is read no more: its slot takes plane ib+3
     if (ib + 3 <= ie + 1) issue_plane(ib + 3);
@@ -474,6 +483,26 @@ __global__ void __launch_bounds__(stage_threads(TJ, TK), stage_min_ctas(sizeof(r
           un[7] += dB2;
           un[4] += w[5] * dB0 + w[6] * dB1 + w[7] * dB2;
         }
+        if (trc) {
+          // CME tracer (Sect. 3.1): rho X carried by each face's mass flux
+          // with X from the face's upwind cell
+          // X at plane i-1 of this column is carried from the previous plane:
+          // that ring slot already receives the copy of plane i+4
+          const int o = (jl + 2) * RK + kl + 2;
+          const real *xc = xslot(i), *xp = xslot(i + 1);
+          const real X0 = xc[o];
+          const real ftl0 = el<real, NTH>(fthb, 0, jl * TK + kl), fth0 = el<real, NTH>(fthb, 0, (jl + 1) * TK + kl);
+          const real fpl0 = el<real, NPH>(fphb, 0, jl * (TK + 1) + kl), fph0 = el<real, NPH>(fphb, 0, jl * (TK + 1) + kl + 1);
+          const real arm = Arm * Flo[0] * (Flo[0] > real(0) ? xprev : X0);
+          const real arp = Arp * Fhi[0] * (Fhi[0] > real(0) ? X0 : xp[o]);
+          const real atm = Atm * ftl0 * (ftl0 > real(0) ? xc[o - RK] : X0);
+          const real atp = Atp * fth0 * (fth0 > real(0) ? X0 : xc[o + RK]);
+          const real apm = Ap * fpl0 * (fpl0 > real(0) ? xc[o - 1] : X0);
+          const real app = Ap * fph0 * (fph0 > real(0) ? X0 : xc[o + 1]);
+          const real dT = -((arp - arm) + (atp - atm) + (app - apm)) * iV;
+          Uout[TRV * vstride + cidx] = U0[TRV * vstride + cidx] + dt * dT;
+          xprev = X0;
+        }
         hits += apply_floors<real>(un, gamma, pfl, rfl, isl);
         if (!(un[0] == un[0]) || !(un[4] == un[4])) atomicOr(kp.status, ST_NAN);
 #pragma unroll
@@ -543,15 +572,22 @@ __global__ void __launch_bounds__(stage_threads(TJ, TK), stage_min_ctas(sizeof(r
   }
 }
 
+// dynamic shared memory limit of both instances of a tile, raised (never
+// lowered) to what a launch needs
 template <typename real, int TJ, int TK>
-int launch_t(const KParams &kp, const StageLaunch &sl, cudaStream_t s) {
-  const size_t smem = StageSmem<real>::bytes(TJ, TK);
-  static bool configured[2] = {false, false};
-  if (!configured[0]) {
+void ensure_smem(size_t smem) {
+  static size_t configured = 0;
+  if (smem > configured) {
     cudaFuncSetAttribute(k_stage<real, TJ, TK, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     cudaFuncSetAttribute(k_stage<real, TJ, TK, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    configured[0] = true;
+    configured = smem;
   }
+}
+
+template <typename real, int TJ, int TK>
+int launch_t(const KParams &kp, const StageLaunch &sl, cudaStream_t s) {
+  const size_t smem = StageSmem<real>::bytes(TJ, TK, kp.nvs > NVAR);
+  ensure_smem<real, TJ, TK>(smem);
   if (sl.stage2)
     k_stage<real, TJ, TK, true><<<sl.grid, stage_threads(TJ, TK), smem, s>>>(kp, sl);
   else
@@ -573,37 +609,36 @@ int dispatch(const KParams &kp, const StageLaunch &sl, cudaStream_t s) {
 }
 
 template <typename real, int TJ, int TK>
-int occupancy_t() {
+int occupancy_t(bool tracer) {
   int n = 0;
-  const size_t smem = StageSmem<real>::bytes(TJ, TK);
-  cudaFuncSetAttribute(k_stage<real, TJ, TK, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  cudaFuncSetAttribute(k_stage<real, TJ, TK, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  const size_t smem = StageSmem<real>::bytes(TJ, TK, tracer);
+  ensure_smem<real, TJ, TK>(smem);
   if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_stage<real, TJ, TK, true>, stage_threads(TJ, TK), smem) != cudaSuccess)
     return 1;
   return n > 0 ? n : 1;
 }
 
 template <typename real>
-int occupancy(int tj, int tk) {
-  if (tj == 8 && tk == 8) return occupancy_t<real, 8, 8>();
-  if (tj == 12 && tk == 12) return occupancy_t<real, 12, 12>();
-  if (tj == 8 && tk == 32) return occupancy_t<real, 8, 32>();
-  if (tj == 4 && tk == 32) return occupancy_t<real, 4, 32>();
-  if (tj == 12 && tk == 20) return occupancy_t<real, 12, 20>();
-  if (tj == 6 && tk == 36) return occupancy_t<real, 6, 36>();
-  if (tj == 10 && tk == 24) return occupancy_t<real, 10, 24>();
-  if (tj == 8 && tk == 24) return occupancy_t<real, 8, 24>();
+int occupancy(int tj, int tk, bool tracer) {
+  if (tj == 8 && tk == 8) return occupancy_t<real, 8, 8>(tracer);
+  if (tj == 12 && tk == 12) return occupancy_t<real, 12, 12>(tracer);
+  if (tj == 8 && tk == 32) return occupancy_t<real, 8, 32>(tracer);
+  if (tj == 4 && tk == 32) return occupancy_t<real, 4, 32>(tracer);
+  if (tj == 12 && tk == 20) return occupancy_t<real, 12, 20>(tracer);
+  if (tj == 6 && tk == 36) return occupancy_t<real, 6, 36>(tracer);
+  if (tj == 10 && tk == 24) return occupancy_t<real, 10, 24>(tracer);
+  if (tj == 8 && tk == 24) return occupancy_t<real, 8, 24>(tracer);
   return 1;
 }
 
 }  // namespace
 
-size_t stage_smem_bytes(int precision, int tj, int tk) {
-  return precision ? StageSmem<float>::bytes(tj, tk) : StageSmem<double>::bytes(tj, tk);
+size_t stage_smem_bytes(int precision, int tj, int tk, int tracer) {
+  return precision ? StageSmem<float>::bytes(tj, tk, tracer) : StageSmem<double>::bytes(tj, tk, tracer);
 }
 
 // an instantiated tile whose shared memory fits one CTA on this device
-int stage_tile_supported(int precision, int tj, int tk) {
+int stage_tile_supported(int precision, int tj, int tk, int tracer) {
   const bool known = (tj == 8 && tk == 8) || (tj == 12 && tk == 12) || (tj == 8 && tk == 32) ||
                      (tj == 4 && tk == 32) || (tj == 12 && tk == 20) || (tj == 6 && tk == 36) ||
                      (tj == 10 && tk == 24) || (tj == 8 && tk == 24);
@@ -612,11 +647,11 @@ int stage_tile_supported(int precision, int tj, int tk) {
   if (cudaGetDevice(&dev) != cudaSuccess ||
       cudaDeviceGetAttribute(&lim, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess)
     return 0;
-  return stage_smem_bytes(precision, tj, tk) <= (size_t)lim;
+  return stage_smem_bytes(precision, tj, tk, tracer) <= (size_t)lim;
 }
 
-int stage_max_ctas_per_sm(int precision, int tj, int tk) {
-  return precision ? occupancy<float>(tj, tk) : occupancy<double>(tj, tk);
+int stage_max_ctas_per_sm(int precision, int tj, int tk, int tracer) {
+  return precision ? occupancy<float>(tj, tk, tracer) : occupancy<double>(tj, tk, tracer);
 }
 
 int stage_launch(const KParams &kp, const StageLaunch &sl, int precision, cudaStream_t s) {

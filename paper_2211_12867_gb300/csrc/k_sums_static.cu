@@ -58,7 +58,7 @@ __global__ void k_block_sums_static(const KParams kp, const real *U, int slot0, 
     const int I = B.ix[0] * kp.nb[0] + i + NGH, J = B.ix[1] * kp.nb[1] + j + NGH;
     const double V = GD.dr3[I] * GD.dcos[J] * GD.dphi;
     for (int v = 0; v < NVAR; v++) {
-      const size_t idx = ((((size_t)slot * NVAR + v) * kp.P[0] + i + NGH) * kp.P[1] + j + NGH) * kp.P[2] + k + NGH;
+      const size_t idx = ((((size_t)slot * kp.nvs + v) * kp.P[0] + i + NGH) * kp.P[1] + j + NGH) * kp.P[2] + k + NGH;
       acc[v] += V * (double)U[idx];
     }
   }

@@ -22,7 +22,7 @@ _lib = None
 FP64, FP32_MIXED = 0, 1
 SPHERICAL, CARTESIAN = 0, 1
 BC_PERIODIC, BC_OUTFLOW, BC_REFLECT, BC_INNER = 0, 1, 2, 3
-FLAG_PLAIN, FLAG_LEARNED, FLAG_BOTH, FLAG_SHOCK = 0, 1, 2, 3
+FLAG_PLAIN, FLAG_LEARNED, FLAG_BOTH, FLAG_SHOCK, FLAG_TRACER, FLAG_COMBINED = 0, 1, 2, 3, 4, 5
 # the shock criterion's windows of the paper (Sect. 3.2): Earth longitude
 # +-30 deg, Earth colatitude +-10 deg, CME longitude +-90 deg
 SHOCK_WINDOWS = (math.radians(30.0), math.radians(10.0), math.radians(90.0))
@@ -38,7 +38,8 @@ EXPORTS = [
     "icarus_set_member_max_level", "icarus_ghost_fill", "icarus_conservation_sums", "icarus_get_dt",
     "icarus_status_word", "icarus_set_tile", "icarus_use_graph", "icarus_kernels_per_step",
     "icarus_profile", "icarus_profile_read", "icarus_set_fp64_islands", "icarus_conservation_sums_static",
-    "icarus_set_floor_budget", "icarus_get_padded", "icarus_set_earth",
+    "icarus_set_floor_budget", "icarus_get_padded", "icarus_set_earth", "icarus_get_tracer",
+    "icarus_set_tracer", "icarus_alu_peak",
     "icarus_mlp_set_params", "icarus_mlp_get_params", "icarus_mlp_features", "icarus_mlp_predict_leaves",
     "icarus_mlp_predict", "icarus_mlp_grad", "icarus_mlp_dataset_clear", "icarus_mlp_dataset_add",
     "icarus_mlp_train", "icarus_cell_updates", "icarus_save", "icarus_load", "icarus_destroy",
@@ -61,7 +62,7 @@ class GridDesc(C.Structure):
         ("p_floor", C.c_double), ("rho_floor", C.c_double),
         ("precision", C.c_int), ("n_members", C.c_int),
         ("bc_lo", C.c_int * 3), ("bc_hi", C.c_int * 3), ("max_blocks", C.c_int),
-        ("arena", C.c_void_p), ("arena_bytes", C.c_size_t), ("stream", C.c_void_p),
+        ("arena", C.c_void_p), ("arena_bytes", C.c_size_t), ("stream", C.c_void_p), ("tracer", C.c_int),
     ]
 
 
@@ -73,7 +74,7 @@ class Refine(C.Structure):
     _fields_ = [("e_refine", C.c_double), ("e_coarsen", C.c_double), ("eps", C.c_double),
                 ("dv", C.c_double), ("mode", C.c_int),
                 ("div_thr", C.c_double), ("dlon_earth", C.c_double), ("dcolat_earth", C.c_double),
-                ("dlon_cme", C.c_double)]
+                ("dlon_cme", C.c_double), ("x_thr", C.c_double)]
 
 
 def load(build_if_missing: bool = True):
@@ -146,7 +147,8 @@ class Icarus:
                  x_min=(0.1, math.pi / 6, 0.0), x_max=(2.0, 5 * math.pi / 6, 2 * math.pi),
                  gamma=1.5, omega=0.0, cfl=0.8, divb_cd=0.8, p_floor=1e-8, rho_floor=1e-8,
                  precision=FP64, n_members=1, bc_lo=(BC_INNER, BC_OUTFLOW, BC_PERIODIC),
-                 bc_hi=(BC_OUTFLOW, BC_OUTFLOW, BC_PERIODIC), max_blocks=0, device=None, stream=None):
+                 bc_hi=(BC_OUTFLOW, BC_OUTFLOW, BC_PERIODIC), max_blocks=0, tracer=False, device=None,
+                 stream=None):
         import torch
         if not torch.cuda.is_available():
             raise RuntimeError("libicarus needs a CUDA GPU; no fallback path exists")
@@ -166,6 +168,7 @@ class Icarus:
         d.bc_lo[:] = list(bc_lo)
         d.bc_hi[:] = list(bc_hi)
         d.max_blocks = max_blocks
+        d.tracer = int(bool(tracer))
         nbytes = C.c_size_t(0)
         _chk("icarus_arena_bytes", self.lib.icarus_arena_bytes(C.byref(d), C.byref(nbytes)))
         self.device = torch.device(device) if device is not None else torch.device("cuda", torch.cuda.current_device())
@@ -235,8 +238,8 @@ class Icarus:
         return out
 
     def flag_refine(self, e_refine=0.1, e_coarsen=0.0125, eps=0.01, dv=0.5, mode=FLAG_PLAIN, div_thr=0.0,
-                    windows=SHOCK_WINDOWS):
-        crit = Refine(e_refine, e_coarsen, eps, dv, mode, div_thr, *windows)
+                    windows=SHOCK_WINDOWS, x_thr=0.0):
+        crit = Refine(e_refine, e_coarsen, eps, dv, mode, div_thr, *windows, x_thr)
         out = np.zeros(self.n_leaves(-1), dtype=np.int8)
         _chk("icarus_flag_refine", self.lib.icarus_flag_refine(self.ctx, C.byref(crit),
                                                                out.ctypes.data_as(C.c_void_p)))
@@ -266,6 +269,22 @@ class Icarus:
         out = np.zeros((n, 8) + self.block)
         _chk("icarus_get_state", self.lib.icarus_get_state(self.ctx, member, _dp(out), out.size))
         return out
+
+    def get_tracer(self, member=0):
+        """CME tracer rho X of a member's interior cells, [leaf][i][j][k]"""
+        out = np.zeros((self.n_leaves(member),) + self.block)
+        f = self.lib.icarus_get_tracer
+        f.restype = C.c_int
+        f.argtypes = [C.c_void_p, C.c_int, C.POINTER(C.c_double), C.c_size_t]
+        _chk("icarus_get_tracer", f(self.ctx, member, _dp(out), out.size))
+        return out
+
+    def set_tracer(self, member, T):
+        T = np.ascontiguousarray(T, dtype=np.float64).reshape((self.n_leaves(member),) + self.block)
+        f = self.lib.icarus_set_tracer
+        f.restype = C.c_int
+        f.argtypes = [C.c_void_p, C.c_int, C.POINTER(C.c_double), C.c_size_t]
+        _chk("icarus_set_tracer", f(self.ctx, member, _dp(T), T.size))
 
     def get_padded(self, member, leaf):
         """a leaf block with its ghost layers as last filled (FP64 conserved)"""
@@ -442,6 +461,17 @@ def conservation_sums_static(g, member=0):
     out = np.zeros(8)
     _chk("icarus_conservation_sums_static", f(g.ctx, member, _dp(out)))
     return out
+
+
+def alu_peak(kind, stream=None):
+    """measured FMA throughput (flop/s): kind 0 FP64, 1 FP32, 2 FP32 packed pairs"""
+    L = load()
+    f = L.icarus_alu_peak
+    f.restype = C.c_int
+    f.argtypes = [C.c_int, C.c_void_p, C.POINTER(C.c_double)]
+    out = C.c_double(0.0)
+    _chk("icarus_alu_peak", f(int(kind), stream, C.byref(out)))
+    return out.value
 
 
 def set_fp64_islands(g, p_over_e=0.05, beta=0.1):

@@ -12,13 +12,13 @@ SPH = dict(x_min=(0.1, math.pi / 6, 0.0), x_max=(1.1, 5 * math.pi / 6, 2 * math.
 
 def make_pair(*, n, nb, x_min=SPH["x_min"], x_max=SPH["x_max"], max_level=1, stretch=False, geometry=0,
               gamma=1.5, omega=I.OMEGA, cfl=0.8, divb_cd=0.8, bc_lo=(3, 1, 0), bc_hi=(1, 1, 0),
-              precision=0, max_blocks=0, n_members=1):
+              precision=0, max_blocks=0, n_members=1, tracer=False):
     from paper_2211_12867_gb300.icarus import Icarus
     g = Icarus(n_cells=n, block=nb, max_level=max_level, stretch=stretch, geometry=geometry, x_min=x_min,
                x_max=x_max, gamma=gamma, omega=omega, cfl=cfl, divb_cd=divb_cd, bc_lo=bc_lo, bc_hi=bc_hi,
-               precision=precision, max_blocks=max_blocks, n_members=n_members)
+               precision=precision, max_blocks=max_blocks, n_members=n_members, tracer=tracer)
     o = O.Grid(geometry=geometry, n=n, nb=nb, max_level=max_level, stretch=int(stretch), xmin=x_min, xmax=x_max,
-               gamma=gamma, omega=omega, cfl=cfl, divb_cd=divb_cd, bc_lo=bc_lo, bc_hi=bc_hi)
+               gamma=gamma, omega=omega, cfl=cfl, divb_cd=divb_cd, bc_lo=bc_lo, bc_hi=bc_hi, tracer=tracer)
     return g, o
 
 

@@ -16,15 +16,16 @@ pytestmark = pytest.mark.gpu
 NONPHYSICAL, STATE = 4, 6
 
 
-def _negative_pressure(g, o, cells=10):
-    """the wind state with `cells` cells of block 3 at pressure -0.5"""
+def _negative_pressure(g, o, cells=10, p=-1e6):
+    """the wind state with `cells` cells of block 3 at pressure p (deep
+    enough that the fluxes cannot refill the cell within one stage)"""
     wind_setup(g, o)
     U = g.get_state(0)
     for q in range(cells):
         i, j, k = 2 + q % 5, 2 + q // 5, 3
         ke = 0.5 * (U[3, 1, i, j, k] ** 2 + U[3, 2, i, j, k] ** 2 + U[3, 3, i, j, k] ** 2) / U[3, 0, i, j, k]
         me = 0.5 * (U[3, 5, i, j, k] ** 2 + U[3, 6, i, j, k] ** 2 + U[3, 7, i, j, k] ** 2)
-        U[3, 4, i, j, k] = ke + me - 0.5 / (g.desc.gamma - 1.0)
+        U[3, 4, i, j, k] = ke + me + p / (g.desc.gamma - 1.0)
     g.set_state(0, U)
 
 
