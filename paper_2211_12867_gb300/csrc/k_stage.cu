@@ -252,19 +252,15 @@ __global__ void __launch_bounds__(stage_threads(TJ, TK), stage_min_ctas(sizeof(r
       ld8<real, RP>(pm, o, a);
       ld8<real, RP>(pc, o, b);
       ld8<real, RP>(pp, o, c);
-#pragma unroll
-      for (int v = 0; v < NVAR; v++) sl_[v] = mc_half_slope<real>(a[v], b[v], c[v]);
+      mc_half_slopes8<real>(a, b, c, sl_);
     };
     // radial face between planes p-1 and p from the slopes at both planes
     auto rflux = [&](int p, const real *sm, const real *sp, real *F) {
       real b[NVAR], c[NVAR], WL[NVAR], WR[NVAR];
       gather(ringp(p - 1), jl + 2, kl + 2, b);
       gather(ringp(p), jl + 2, kl + 2, c);
-#pragma unroll
-      for (int v = 0; v < NVAR; v++) {
-        WL[v] = b[v] + sm[v];
-        WR[v] = c[v] - sp[v];
-      }
+      axpy8<real>(b, real(1), sm, WL);
+      axpy8<real>(c, real(-1), sp, WR);
       tvdlf_states<real, 0>(WL, WR, b, c, gamma, igm1, F);
     };
     // div B at plane p on the (TJ+2) x (TK+2) positions around the tile
@@ -406,9 +402,13 @@ __global__ void __launch_bounds__(stage_threads(TJ, TK), stage_min_ctas(sizeof(r
       if (valid) {
         const int pr = i - ib + 2, jr = jl + 2;   // indices in the staged arrays
         const real dcos = s_dcos[jr], dr2 = s_dr2[pr];
+        // face areas; the fluxes carry a factor 2 (tvdlf_states), which the
+        // half areas hArm ... hAp take back
         const real Arm = s_r2f[pr] * dcos * dphi, Arp = s_r2f[pr + 1] * dcos * dphi;
         const real Atm = s_sinf[jr] * dr2 * dphi, Atp = s_sinf[jr + 1] * dr2 * dphi;
         const real Ap = dr2 * s_dth[jr];
+        const real hArm = real(0.5) * Arm, hArp = real(0.5) * Arp, hAtm = real(0.5) * Atm, hAtp = real(0.5) * Atp,
+                   hAp = real(0.5) * Ap;
         const real V = s_dr3[pr] * dcos * dphi;
         const real iV = RT<real>::rcp_(V);
         real w[NVAR];
@@ -429,7 +429,7 @@ __global__ void __launch_bounds__(stage_threads(TJ, TK), stage_min_ctas(sizeof(r
 #pragma unroll
             for (int h = 0; h < CH; h++) {
               const int v = c * CH + h;
-              const real div = (Arp * Fhi[v] - Arm * Flo[v]) + (Atp * fth_[h] - Atm * ftl[h]) + Ap * (fph_[h] - fpl[h]);
+              const real div = (hArp * Fhi[v] - hArm * Flo[v]) + (hAtp * fth_[h] - hAtm * ftl[h]) + hAp * (fph_[h] - fpl[h]);
               un[v] = -div * iV;
             }
           }
@@ -493,12 +493,12 @@ __global__ void __launch_bounds__(stage_threads(TJ, TK), stage_min_ctas(sizeof(r
           const real X0 = xc[o];
           const real ftl0 = el<real, NTH>(fthb, 0, jl * TK + kl), fth0 = el<real, NTH>(fthb, 0, (jl + 1) * TK + kl);
           const real fpl0 = el<real, NPH>(fphb, 0, jl * (TK + 1) + kl), fph0 = el<real, NPH>(fphb, 0, jl * (TK + 1) + kl + 1);
-          const real arm = Arm * Flo[0] * (Flo[0] > real(0) ? xprev : X0);
-          const real arp = Arp * Fhi[0] * (Fhi[0] > real(0) ? X0 : xp[o]);
-          const real atm = Atm * ftl0 * (ftl0 > real(0) ? xc[o - RK] : X0);
-          const real atp = Atp * fth0 * (fth0 > real(0) ? X0 : xc[o + RK]);
-          const real apm = Ap * fpl0 * (fpl0 > real(0) ? xc[o - 1] : X0);
-          const real app = Ap * fph0 * (fph0 > real(0) ? X0 : xc[o + 1]);
+          const real arm = hArm * Flo[0] * (Flo[0] > real(0) ? xprev : X0);
+          const real arp = hArp * Fhi[0] * (Fhi[0] > real(0) ? X0 : xp[o]);
+          const real atm = hAtm * ftl0 * (ftl0 > real(0) ? xc[o - RK] : X0);
+          const real atp = hAtp * fth0 * (fth0 > real(0) ? X0 : xc[o + RK]);
+          const real apm = hAp * fpl0 * (fpl0 > real(0) ? xc[o - 1] : X0);
+          const real app = hAp * fph0 * (fph0 > real(0) ? X0 : xc[o + 1]);
           const real dT = -((arp - arm) + (atp - atm) + (app - apm)) * iV;
           Uout[TRV * vstride + cidx] = U0[TRV * vstride + cidx] + dt * dT;
           xprev = X0;
@@ -531,27 +531,27 @@ __global__ void __launch_bounds__(stage_threads(TJ, TK), stage_min_ctas(sizeof(r
             // r faces
             if (i == 0 && (B.nbr[0] == NB_COARSER || B.nbr[0] == NB_FINER))
 #pragma unroll
-              for (int v = 0; v < NVAR; v++) fb[(size_t)v * fc0 + j * nb2 + k] = Arm * Flo[v];
+              for (int v = 0; v < NVAR; v++) fb[(size_t)v * fc0 + j * nb2 + k] = hArm * Flo[v];
             if (i == nb0 - 1 && (B.nbr[1] == NB_COARSER || B.nbr[1] == NB_FINER))
 #pragma unroll
-              for (int v = 0; v < NVAR; v++) fb[(size_t)NVAR * fc0 + (size_t)v * fc0 + j * nb2 + k] = Arp * Fhi[v];
+              for (int v = 0; v < NVAR; v++) fb[(size_t)NVAR * fc0 + (size_t)v * fc0 + j * nb2 + k] = hArp * Fhi[v];
             const size_t o2 = (size_t)2 * NVAR * fc0, o4 = o2 + (size_t)2 * NVAR * fc1;
             if (j == 0 && (B.nbr[2] == NB_COARSER || B.nbr[2] == NB_FINER))
 #pragma unroll
               for (int v = 0; v < NVAR; v++)
-                fb[o2 + (size_t)v * fc1 + i * nb2 + k] = Atm * el<real, NTH>(fthb, v, jl * TK + kl);
+                fb[o2 + (size_t)v * fc1 + i * nb2 + k] = hAtm * el<real, NTH>(fthb, v, jl * TK + kl);
             if (j == nb1 - 1 && (B.nbr[3] == NB_COARSER || B.nbr[3] == NB_FINER))
 #pragma unroll
               for (int v = 0; v < NVAR; v++)
-                fb[o2 + (size_t)NVAR * fc1 + (size_t)v * fc1 + i * nb2 + k] = Atp * el<real, NTH>(fthb, v, (jl + 1) * TK + kl);
+                fb[o2 + (size_t)NVAR * fc1 + (size_t)v * fc1 + i * nb2 + k] = hAtp * el<real, NTH>(fthb, v, (jl + 1) * TK + kl);
             if (k == 0 && (B.nbr[4] == NB_COARSER || B.nbr[4] == NB_FINER))
 #pragma unroll
               for (int v = 0; v < NVAR; v++)
-                fb[o4 + (size_t)v * fc2 + i * nb1 + j] = Ap * el<real, NPH>(fphb, v, jl * (TK + 1) + kl);
+                fb[o4 + (size_t)v * fc2 + i * nb1 + j] = hAp * el<real, NPH>(fphb, v, jl * (TK + 1) + kl);
             if (k == nb2 - 1 && (B.nbr[5] == NB_COARSER || B.nbr[5] == NB_FINER))
 #pragma unroll
               for (int v = 0; v < NVAR; v++)
-                fb[o4 + (size_t)NVAR * fc2 + (size_t)v * fc2 + i * nb1 + j] = Ap * el<real, NPH>(fphb, v, jl * (TK + 1) + kl + 1);
+                fb[o4 + (size_t)NVAR * fc2 + (size_t)v * fc2 + i * nb1 + j] = hAp * el<real, NPH>(fphb, v, jl * (TK + 1) + kl + 1);
           }
         }
 #pragma unroll

@@ -92,9 +92,10 @@ def test_checkpoint_without_preflagger_clears_the_loaded_one(tmp_path):
         h.mlp_predict(np.zeros((4, 64), np.float32))
 
 
-def _ck_rows_offset(nfp=29):
+def _ck_rows_offset(raw):
     # magic, version, field count, descriptor fields, then member 0's
     # (max level, leaf count) and its cone CME record (8 doubles, 2 ints)
+    nfp = int(np.frombuffer(bytes(raw[12:16]), dtype=np.uint32)[0])
     return 8 + 4 + 4 + 8 * nfp + 8 + 72
 
 
@@ -106,13 +107,14 @@ def test_corrupt_trees_are_refused(tmp_path):
     path = tmp_path / "f.ck"
     g.save(str(path))
     raw = bytearray(path.read_bytes())
-    rows = np.frombuffer(bytes(raw[_ck_rows_offset():_ck_rows_offset() + 16 * 32]), dtype=np.int32).reshape(32, 4)
+    off = _ck_rows_offset(raw)
+    rows = np.frombuffer(bytes(raw[off:off + 16 * 32]), dtype=np.int32).reshape(32, 4)
     assert np.array_equal(rows, g.tree(0))          # the offsets above are right
     dup = bytearray(raw)
-    dup[_ck_rows_offset() + 16:_ck_rows_offset() + 32] = raw[_ck_rows_offset():_ck_rows_offset() + 16]
+    dup[off + 16:off + 32] = raw[off:off + 16]
     (tmp_path / "dup.ck").write_bytes(bytes(dup))
     big = bytearray(raw)
-    big[_ck_rows_offset() - 76:_ck_rows_offset() - 72] = np.int32(2 ** 30).tobytes()
+    big[off - 76:off - 72] = np.int32(2 ** 30).tobytes()
     (tmp_path / "big.ck").write_bytes(bytes(big))
     h, _ = make_pair(n=(48, 16, 32), nb=(12, 8, 8))
     wind_setup(h, _)

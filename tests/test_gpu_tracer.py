@@ -81,12 +81,13 @@ def test_tracer_and_combined_flags_bit_exact(precision):
     g, o = _cme_pair(precision=precision, max_level=3, max_blocks=4000)
     g.set_earth(0, math.pi / 2, math.pi, 0.0, I.OMEGA_SYN)
     o.set_earth(math.pi / 2, math.pi, 0.0, I.OMEGA_SYN)
-    g.step(40)
+    g.step(12)
     for mode, kw in ((FLAG_TRACER, dict(windows=(0.0, 0.0, 0.0))), (FLAG_TRACER, dict(x_thr=0.1)),
                      (FLAG_COMBINED, dict()), (FLAG_COMBINED, dict(x_thr=0.5, div_thr=1.0))):
         fg, fo = _flags_same_state(g, o, mode, **kw)
         assert np.array_equal(fg, fo), (mode, kw)
-    fg, _ = _flags_same_state(g, o, FLAG_TRACER, windows=(0.0, 0.0, 0.0))
+    # the CME plasma (X near 1) fills only part of the grid after 12 steps
+    fg, _ = _flags_same_state(g, o, FLAG_TRACER, windows=(0.0, 0.0, 0.0), x_thr=0.1)
     assert (fg == 1).sum() > 0 and (fg == -1).sum() > 0
 
 
