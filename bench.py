@@ -66,7 +66,8 @@ def parse():
     p.add_argument("--islands", default="0.002,0.1",
                    help="FP32 mode: FP64 pressure where p < a*e or p < b*B^2/2 ('a,b')")
     p.add_argument("--tile", default="", help="force the stage tile 'tile_theta,tile_phi,r_segment'")
-    p.add_argument("--workload", default="wedge", choices=["wedge", "amr", "ensemble", "tt1au", "learned5", "series"],
+    p.add_argument("--workload", default="wedge",
+                   choices=["wedge", "amr", "ensemble", "tt1au", "learned5", "series", "ladder"],
                    help="amr / ensemble / tt1au: stretched AMR CME runs (one JSON line of their own)")
     p.add_argument("--members", type=int, default=32)
     p.add_argument("--max-blocks", type=int, default=60000)
@@ -79,6 +80,9 @@ def parse():
     p.add_argument("--hours", type=float, default=72.0)
     p.add_argument("--relax-days", type=float, default=10.0)
     p.add_argument("--regrid-every", type=int, default=10)
+    p.add_argument("--rungs", default="low_str,middle_str,middle_eq,shock2,shock3,shock4,shock5,tracer2,tracer3,"
+                   "combined2,combined3,combined4,combined5",
+                   help="ladder: the single-level grids and <criterion><level> AMR runs on the Low stretched grid")
     p.add_argument("--mode", default="full", choices=["full", "kernel"],
                    help="kernel: set up and run warmup + steps only (for profiler captures)")
     return p.parse_args()
@@ -487,6 +491,44 @@ def run_series_workload(args):
     return 0
 
 
+def run_ladder_workload(args):
+    """The resolution ladder of the paper's comparison on the synthetic wind
+    and cone CME: single-level Low/Middle stretched and Middle equidistant
+    grids (Table 1), then AMR levels 2-5 on the Low stretched base grid with
+    the tracer (Sect. 3.1), shock (Sect. 3.2) and combined (Sect. 3.3)
+    criteria.  One JSON line per rung, then a summary line with speed-ups
+    against the Middle grids (the shape of Tables 4-6)."""
+    import torch
+    from paper_2211_12867_gb300 import workloads as WL
+    from paper_2211_12867_gb300.icarus import FP32_MIXED, FP64
+    torch.cuda.set_device(0)
+    prec = FP32_MIXED if args.precision == "fp32" else FP64
+    out = {}
+    for rung in args.rungs.split(","):
+        if rung in WL.LADDER_GRIDS:
+            rep = WL.run_ladder_case(rung, None, 1, relax_days=args.relax_days, hours_after=args.hours,
+                                     precision=prec)
+        else:
+            kind, level = rung.rstrip("0123456789"), int(rung[len(rung.rstrip("0123456789")):])
+            rep = WL.run_ladder_case("low_str", kind, level, relax_days=args.relax_days, hours_after=args.hours,
+                                     regrid_every=args.regrid_every, precision=prec, max_blocks=args.max_blocks)
+        out[rung] = rep
+        print(json.dumps({"rung": rung, **rep}), flush=True)
+    summ = {}
+    for rung, rep in out.items():
+        row = {"wall_s": rep["wall_s"], "time_to_arrival_s": rep["time_to_arrival_s"],
+               "arrival_h": rep["arrival_h"][0], "shock_width_h": rep["shock_width_h"][0],
+               "peak_speed_kms": rep["peak_speed_kms"][0], "leaves_max": rep["leaves_max"],
+               "cell_updates_per_s": rep["cell_updates_per_s"]}
+        for ref in ("middle_eq", "middle_str"):
+            if ref in out and rep["wall_s"] > 0:
+                row[f"speedup_vs_{ref}"] = out[ref]["wall_s"] / rep["wall_s"]
+        summ[rung] = row
+    print(json.dumps({"workload": "ladder", "precision": args.precision, "hours_after_injection": args.hours,
+                      "rungs": summ}), flush=True)
+    return 0
+
+
 def main():
     args = parse()
     if args.impl == "reference":
@@ -501,6 +543,8 @@ def main():
         return run_learned5_workload(args)
     if args.workload == "series":
         return run_series_workload(args)
+    if args.workload == "ladder":
+        return run_ladder_workload(args)
     import torch
     from paper_2211_12867_gb300.replicas import ReplicaGroup
     grp = ReplicaGroup("nccl")
@@ -600,7 +644,7 @@ def main():
     # ---- end to end through the public API, host buffers ----
     from paper_2211_12867_gb300.icarus import Icarus  # noqa: F401
     pin_state = torch.empty(W0.size, dtype=torch.float64).pin_memory().numpy().reshape(W0.shape)
-    pin_state[...] = g.get_state(0)
+    g.get_state(0, out=pin_state)
     pin_out = torch.empty(W0.size, dtype=torch.float64).pin_memory().numpy().reshape(W0.shape)
     t_now = float(g.step(0)[0])
     earth = I.earth_position(t_now, 0.0)
@@ -610,7 +654,7 @@ def main():
     for s in range(args.steps):
         g.step(1, t_stop=np.inf)                    # h2d t_stop, d2h member time
         g.probe(0, earth[None, :])                  # h2d probe point, d2h 8 primitives
-    pin_out[...] = g.get_state(0)                   # d2h: the job's output state
+    g.get_state(0, out=pin_out)                     # d2h: the job's output state
     torch.cuda.synchronize()
     barrier()
     e2e_s = grp.max_over_ranks(time.perf_counter() - w0)

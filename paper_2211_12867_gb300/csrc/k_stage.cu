@@ -426,12 +426,8 @@ __global__ void __launch_bounds__(stage_threads(TJ, TK), stage_min_ctas(sizeof(r
             V::put(*reinterpret_cast<const typename V::T *>(fthb + (c * NTH + qt + TK) * CH), fth_);
             V::put(*reinterpret_cast<const typename V::T *>(fphb + (c * NPH + qp) * CH), fpl);
             V::put(*reinterpret_cast<const typename V::T *>(fphb + (c * NPH + qp + 1) * CH), fph_);
-#pragma unroll
-            for (int h = 0; h < CH; h++) {
-              const int v = c * CH + h;
-              const real div = (hArp * Fhi[v] - hArm * Flo[v]) + (hAtp * fth_[h] - hAtm * ftl[h]) + hAp * (fph_[h] - fpl[h]);
-              un[v] = -div * iV;
-            }
+            flux_balance<real, CH>(Fhi + c * CH, Flo + c * CH, fth_, ftl, fph_, fpl, hArp, hArm, hAtp, hAtm, hAp,
+                                   iV, un + c * CH);
           }
         }
         if (spherical) {
@@ -451,8 +447,12 @@ __global__ void __launch_bounds__(stage_threads(TJ, TK), stage_min_ctas(sizeof(r
           un[4] += rho * Om * Om * rc * st * vs;
         }
         cp_async_wait_group<0>();   // this thread's U^n copy of plane i
+        {
+          real u0[NVAR];
 #pragma unroll
-        for (int v = 0; v < NVAR; v++) un[v] = u0s[v * NT + tid] + dt * un[v];
+          for (int v = 0; v < NVAR; v++) u0[v] = u0s[v * NT + tid];
+          axpy8<real>(u0, dt, un, un);
+        }
         if (S2 && Cd > real(0)) {
           const real *dm = dring + ((i - 1) & 3) * DP, *dc = dring + (i & 3) * DP, *dp = dring + ((i + 1) & 3) * DP;
           const int q = (jl + 1) * DK + (kl + 1);

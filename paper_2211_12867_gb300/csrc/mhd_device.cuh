@@ -215,6 +215,17 @@ __device__ __forceinline__ void axpy8<float>(const float *a, float s, const floa
   }
 }
 
+// Half MC slope from the one-sided differences dm, dp and their sum s, by
+// sign arithmetic: with sigma the sign of s, the slope is
+// sigma * max(0, min(sigma dm, sigma dp, |s| / 4)) -- zero unless dm and dp
+// share s's sign, the same value as mc_half_slope (bar the sign of a zero).
+__device__ __forceinline__ float half_mc_signed(float dm, float dp, float s) {
+  const unsigned sg = __float_as_uint(s) & 0x80000000u;
+  const float a = __uint_as_float(__float_as_uint(dm) ^ sg), b = __uint_as_float(__float_as_uint(dp) ^ sg);
+  const float m = fmaxf(fminf(fminf(a, b), 0.25f * fabsf(s)), 0.f);
+  return __uint_as_float(__float_as_uint(m) | sg);
+}
+
 // Half the monotonised-central slopes of the 8 variables at the middle of
 // three cells (see mc_half_slope); the differences go in packed pairs in
 // FP32 mode.
@@ -232,10 +243,42 @@ __device__ __forceinline__ void mc_half_slopes8<float>(const float *um, const fl
     const float2 dm = __fadd2_rn(c, make_float2(-um[v], -um[v + 1]));
     const float2 dp = __fadd2_rn(make_float2(up[v], up[v + 1]), make_float2(-c.x, -c.y));
     const float2 sm = __fadd2_rn(dm, dp);
-    const float l0 = fminf(fminf(fabsf(dm.x), fabsf(dp.x)), 0.25f * fabsf(sm.x));
-    const float l1 = fminf(fminf(fabsf(dm.y), fabsf(dp.y)), 0.25f * fabsf(sm.y));
-    out[v] = dm.x * dp.x > 0.f ? copysignf(l0, sm.x) : 0.f;
-    out[v + 1] = dm.y * dp.y > 0.f ? copysignf(l1, sm.y) : 0.f;
+    out[v] = half_mc_signed(dm.x, dp.x, sm.x);
+    out[v + 1] = half_mc_signed(dm.y, dp.y, sm.y);
+  }
+}
+
+// Flux balance of CH variables of a cell: out[h] = -((Arp Fhi - Arm Flo) +
+// (Atp Fth - Atm Ftl) + Ap (Fph - Fpl)) * iV, FP32 in packed pairs.
+template <typename real, int CH>
+__device__ __forceinline__ void flux_balance(const real *Fhi, const real *Flo, const real *fth, const real *ftl,
+                                             const real *fph, const real *fpl, real Arp, real Arm, real Atp,
+                                             real Atm, real Ap, real iV, real *out) {
+#pragma unroll
+  for (int h = 0; h < CH; h++) {
+    const real div = (Arp * Fhi[h] - Arm * Flo[h]) + (Atp * fth[h] - Atm * ftl[h]) + Ap * (fph[h] - fpl[h]);
+    out[h] = -div * iV;
+  }
+}
+template <>
+__device__ __forceinline__ void flux_balance<float, 4>(const float *Fhi, const float *Flo, const float *fth,
+                                                       const float *ftl, const float *fph, const float *fpl,
+                                                       float Arp, float Arm, float Atp, float Atm, float Ap,
+                                                       float iV, float *out) {
+  const float2 arp = make_float2(Arp, Arp), narm = make_float2(-Arm, -Arm), atp = make_float2(Atp, Atp),
+               natm = make_float2(-Atm, -Atm), ap = make_float2(Ap, Ap), m1 = make_float2(-1.f, -1.f),
+               niv = make_float2(-iV, -iV);
+#pragma unroll
+  for (int h = 0; h < 4; h += 2) {
+    const float2 r = __ffma2_rn(narm, make_float2(Flo[h], Flo[h + 1]),
+                                __fmul2_rn(arp, make_float2(Fhi[h], Fhi[h + 1])));
+    const float2 t = __ffma2_rn(natm, make_float2(ftl[h], ftl[h + 1]),
+                                __fmul2_rn(atp, make_float2(fth[h], fth[h + 1])));
+    const float2 p = __ffma2_rn(m1, make_float2(fpl[h], fpl[h + 1]), make_float2(fph[h], fph[h + 1]));
+    const float2 d = __ffma2_rn(ap, p, __fadd2_rn(r, t));
+    const float2 o = __fmul2_rn(d, niv);
+    out[h] = o.x;
+    out[h + 1] = o.y;
   }
 }
 

@@ -264,9 +264,14 @@ class Icarus:
         U = np.ascontiguousarray(U, dtype=np.float64).reshape((n, 8) + self.block)
         _chk("icarus_set_state", self.lib.icarus_set_state(self.ctx, member, _dp(U), U.size, int(bool(prim))))
 
-    def get_state(self, member=0):
+    def get_state(self, member=0, out=None):
+        """conserved state of a member (host FP64); `out` (optional, e.g. a
+        pinned buffer) receives it in place"""
         n = self.n_leaves(member)
-        out = np.zeros((n, 8) + self.block)
+        if out is None:
+            out = np.zeros((n, 8) + self.block)
+        elif out.shape != (n, 8) + self.block or out.dtype != np.float64 or not out.flags.c_contiguous:
+            raise ValueError("get_state: out must be a C-contiguous float64 array of the state's shape")
         _chk("icarus_get_state", self.lib.icarus_get_state(self.ctx, member, _dp(out), out.size))
         return out
 

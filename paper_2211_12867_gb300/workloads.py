@@ -7,6 +7,10 @@
             Loehner + speed-gate criterion, regrid every 10 steps.
 * ensemble — 32 cone-CME draws on the amr grid, levels 3 or 4 per member.
 * learned — the amr grid at level 5 with the learned pre-flagger.
+* ladder  — the resolution ladder of the paper's comparison (Sects. 3.1-3.3,
+            Tables 1, 4-6): the Low and Middle stretched grids, the Middle
+            equidistant grid, and AMR levels 2-5 on the Low stretched base
+            grid with the tracer, shock and combined criteria.
 
 Relaxation: the wind runs from the spherical start state until the slow
 stream has crossed the domain (reading R14: 10 days for 0.1-2 AU; the paper
@@ -156,3 +160,58 @@ def run_learned_window(g, *, n_regrids, regrid_every, max_level, crit=None, t_st
             "extra_preflags": int(sum(int((r["learned"] > 0).sum() - (r["plain"] > 0).sum()) for r in recs)),
             "missed_refinable_plain": float(np.mean(mp)) if mp else None,
             "missed_refinable_learned": float(np.mean(ml)) if ml else None, "judged_regrids": len(mp)}
+
+
+# ---- resolution ladder (Table 1 grids; Sects. 3.1-3.3) ----
+LADDER_GRIDS = {
+    # name: (cells r, theta, phi), radially stretched, block
+    "low_str": ((60, 32, 96), True, (12, 8, 12)),
+    "middle_str": ((120, 64, 192), True, (12, 8, 12)),
+    "middle_eq": ((600, 64, 192), False, (24, 16, 48)),
+}
+
+
+def ladder_grid(name, max_level=1, precision=FP32_MIXED, tracer=False, max_blocks=60000):
+    cells, stretch, block = LADDER_GRIDS[name]
+    return Icarus(n_cells=cells, block=block, max_level=max_level, stretch=stretch, x_min=X_MIN, x_max=X_MAX,
+                  omega=I.OMEGA, cfl=0.8, divb_cd=0.8, precision=precision, max_blocks=max_blocks,
+                  tracer=tracer)
+
+
+def ladder_crit(kind):
+    """refinement criterion of a ladder run: 'shock' (Sect. 3.2: div v < 0 in
+    the Earth and CME windows), 'tracer' (Sect. 3.1: X > 0, no windows) or
+    'combined' (Sect. 3.3: either, in the windows)"""
+    from .icarus import FLAG_COMBINED, FLAG_SHOCK, FLAG_TRACER, SHOCK_WINDOWS
+    if kind == "shock":
+        return dict(mode=FLAG_SHOCK, div_thr=0.0, windows=SHOCK_WINDOWS)
+    if kind == "tracer":
+        return dict(mode=FLAG_TRACER, x_thr=0.0, windows=(0.0, 0.0, 0.0))
+    if kind == "combined":
+        return dict(mode=FLAG_COMBINED, x_thr=0.0, div_thr=0.0, windows=SHOCK_WINDOWS)
+    raise ValueError(kind)
+
+
+def run_ladder_case(grid, kind=None, max_level=1, *, relax_days=10.0, hours_after=60.0, regrid_every=10,
+                    precision=FP32_MIXED, earth_lon0=math.pi, max_blocks=60000):
+    """One rung: relax the seeded wind on the base grid, inject the cone CME
+    of the 512 x 60 x 180 workload, propagate with Earth probes every 10
+    minutes (regridding with criterion `kind` when max_level > 1); returns a
+    JSON-ready report with the wall clock from injection to the end and to
+    the shock's arrival."""
+    tracer = kind in ("tracer", "combined")
+    g = ladder_grid(grid, max_level=max_level, precision=precision, tracer=tracer, max_blocks=max_blocks)
+    start_wind(g)
+    t_inj, wall_relax = relax(g, relax_days)
+    g.set_earth(0, 0.5 * math.pi, earth_lon0, t_inj, I.OMEGA_SYN)
+    ups0 = float(np.sum(g.cell_updates()))
+    crit = ladder_crit(kind) if max_level > 1 else None
+    res = H.propagate(g, [I.cme_config2(seed=0, earth_lon=earth_lon0)], t_inj=t_inj,
+                      duration=I.hours(hours_after), regrid_every=regrid_every if max_level > 1 else 0,
+                      crit=crit, earth_lon0=earth_lon0)
+    rep = amr_report(g, res, wall_relax, t_inj, ups0)
+    rep.update({"grid": grid, "cells": list(LADDER_GRIDS[grid][0]), "stretched": LADDER_GRIDS[grid][1],
+                "max_level": max_level, "criterion": kind, "time_to_arrival_s": res.wall_to(res.arrival[0]),
+                "relax_days": relax_days, "hours_after_injection": hours_after})
+    del g
+    return rep
