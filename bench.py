@@ -72,6 +72,7 @@ def parse():
     p.add_argument("--members", type=int, default=32)
     p.add_argument("--max-blocks", type=int, default=60000)
     p.add_argument("--train-regrids", type=int, default=60)
+    p.add_argument("--train-draws", type=int, default=3, help="tt1au: CME draws the pre-flagger is trained on")
     p.add_argument("--batch", type=int, default=8, help="tt1au: members of the batched learned arm")
     p.add_argument("--window-regrids", type=int, default=60, help="learned5: regrids after injection")
     p.add_argument("--arms", default="fp32_learned,fp32_plain,fp64_plain",
@@ -80,6 +81,8 @@ def parse():
     p.add_argument("--hours", type=float, default=72.0)
     p.add_argument("--relax-days", type=float, default=10.0)
     p.add_argument("--regrid-every", type=int, default=10)
+    p.add_argument("--max-wall", type=float, default=None,
+                   help="ensemble: end the propagation after this many wall-clock seconds (reported)")
     p.add_argument("--rungs", default="low_str,middle_str,middle_eq,shock2,shock3,shock4,shock5,tracer2,tracer3,"
                    "combined2,combined3,combined4,combined5",
                    help="ladder: the single-level grids and <criterion><level> AMR runs on the Low stretched grid")
@@ -311,9 +314,11 @@ def run_ensemble_workload(args):
     ups0 = float(np.sum(g.cell_updates()))
     res = WL.run_cme(g, draws, t_inj=t_inj, hours_after=args.hours, regrid_every=args.regrid_every,
                      max_levels=[d["max_level"] for d in draws], stop_hours_after_arrival=6.0,
-                     progress=sys.stderr)
+                     progress=sys.stderr, max_wall_s=args.max_wall)
     rep = WL.amr_report(g, res, wall_relax, t_inj, ups0)
     name = f"ensemble{args.members}_amr264x36x96"
+    rep["simulated_hours"] = float((res.times[-1] - t_inj) / I.hours(1.0))
+    rep["arrived"] = int(sum(a is not None for a in res.arrival))
     print(json.dumps({"workload": name, "precision": "fp32", "hours_after_injection": args.hours,
                       "max_levels": [d["max_level"] for d in draws],
                       "speeds_kms": [d["v"] * 100.0 for d in draws], **rep}), flush=True)
@@ -331,14 +336,22 @@ def run_tt1au_workload(args):
     from paper_2211_12867_gb300.icarus import FP32_MIXED, FP64
     torch.cuda.set_device(0)
     L = args.max_level
-    # training data: FP32 run with a different CME draw
-    g = WL.amr_grid(max_level=L, precision=FP32_MIXED, max_blocks=args.max_blocks)
-    WL.start_wind(g)
-    t_inj, _ = WL.relax(g, args.relax_days)
-    g.inject_cone_cme(0, t_start=t_inj, **I.cme_config2(seed=7))
-    # labels one regrid ahead at the interval the learned run uses
-    recs = H.collect_regrids(g, n_regrids=args.train_regrids, regrid_every=2 * args.regrid_every, crit=WL.CRIT)
-    X0, T0 = H.training_pairs(recs, max_level=L)
+    # training data: FP32 runs of other CME draws (seeds 7, 8, ...), labels
+    # one regrid ahead at the interval the learned run uses
+    Xs, Ts = [], []
+    for seed in range(7, 7 + args.train_draws):
+        g = WL.amr_grid(max_level=L, precision=FP32_MIXED, max_blocks=args.max_blocks)
+        WL.start_wind(g)
+        t_inj, _ = WL.relax(g, args.relax_days)
+        g.inject_cone_cme(0, t_start=t_inj, **I.cme_config2(seed=seed))
+        recs = H.collect_regrids(g, n_regrids=args.train_regrids, regrid_every=2 * args.regrid_every,
+                                 crit=WL.CRIT)
+        x, t = H.training_pairs(recs, max_level=L)
+        Xs.append(x)
+        Ts.append(t)
+        if seed < 6 + args.train_draws:
+            del g
+    X0, T0 = np.concatenate(Xs), np.concatenate(Ts)
     pos_frac = float(T0.mean())
     X, T = H.rebalance(X0, T0, seed=2)
     g.mlp_set_params(I.mlp_init(5).astype(np.float32))
@@ -368,9 +381,13 @@ def run_tt1au_workload(args):
         ups0 = float(np.sum(g.cell_updates()))
         # a batch holds nm copies of the same CME run (the time per instance
         # is the batch's wall clock / nm)
+        recs = [] if nm == 1 and prec == FP32_MIXED else None
         res = WL.run_cme(g, [I.cme_config2(seed=0)] * nm, t_inj=t_inj, hours_after=args.hours,
-                         regrid_every=every, learned=learned)
+                         regrid_every=every, learned=learned, records=recs)
         rep = WL.amr_report(g, res, wall_relax, t_inj, ups0)
+        if recs:
+            rep["missed_refinable_by_level"] = H.missed_by_level(recs, L, "applied")
+            rep["regrid_every"] = every
         rep["members"] = nm
         rep["time_to_arrival_s"] = res.wall_to(res.arrival[0])
         if rep["time_to_arrival_s"] is not None:
@@ -392,6 +409,7 @@ def run_tt1au_workload(args):
             serr[key + "_max_abs_diff"] = float(np.max(np.abs(x - y)))
             serr[key + "_max_rel_diff"] = float(np.max(np.abs(x - y)) / np.max(np.abs(y)))
     print(json.dumps({"workload": f"tt1au_amr264x36x96_L{L}", "train_pairs": int(len(T)),
+                      "train_draws": args.train_draws,
                       "label_positive_fraction": pos_frac, "threshold": thr, "train_f1": f1,
                       "train_loss": [float(losses[0]), float(losses[-1])], "train_s": train_s, **out,
                       "fp32_vs_fp64_series": serr,
@@ -516,12 +534,15 @@ def run_ladder_workload(args):
         print(json.dumps({"rung": rung, **rep}), flush=True)
     summ = {}
     for rung, rep in out.items():
+        if "error" in rep:
+            summ[rung] = {"error": rep["error"], "status_word": rep["status_word"]}
+            continue
         row = {"wall_s": rep["wall_s"], "time_to_arrival_s": rep["time_to_arrival_s"],
                "arrival_h": rep["arrival_h"][0], "shock_width_h": rep["shock_width_h"][0],
                "peak_speed_kms": rep["peak_speed_kms"][0], "leaves_max": rep["leaves_max"],
                "cell_updates_per_s": rep["cell_updates_per_s"]}
         for ref in ("middle_eq", "middle_str"):
-            if ref in out and rep["wall_s"] > 0:
+            if ref in out and "wall_s" in out[ref] and rep["wall_s"] > 0:
                 row[f"speedup_vs_{ref}"] = out[ref]["wall_s"] / rep["wall_s"]
         summ[rung] = row
     print(json.dumps({"workload": "ladder", "precision": args.precision, "hours_after_injection": args.hours,

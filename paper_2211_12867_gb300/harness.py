@@ -111,6 +111,24 @@ def missed_flag_rate(tree_k, preflag_k, tree_k1, flags_k1, max_level=None):
     return (missed / need) if need else None
 
 
+def missed_by_level(recs, max_level, key):
+    """Missed-refinement rate per level over consecutive regrid records
+    (tree, pre-flags under `key`, plain flags): the share of the leaves the
+    plain estimator flags +1 at regrid k+1 (and that can still refine) whose
+    region the pre-flags of regrid k did not flag; {level: rate or None}."""
+    need, missed = {}, {}
+    for a, b in zip(recs[:-1], recs[1:]):
+        pre = a[key] > 0
+        for (l, _, _, _), hits, f in zip(b["tree"], _related(a["tree"], b["tree"]), b["plain"]):
+            l = int(l)
+            if l >= max_level or f <= 0:
+                continue
+            need[l] = need.get(l, 0) + 1
+            if not any(pre[h] for h in hits):
+                missed[l] = missed.get(l, 0) + 1
+    return {L: (missed.get(L, 0) / need[L] if need.get(L) else None) for L in range(1, max_level)}
+
+
 def collect_regrids(g, n_regrids, regrid_every, t_stop=np.inf, crit=None):
     """Advance with plain regrids and record, at every regrid, the tree of
     member 0, the features of its leaves and the plain flags."""
@@ -242,12 +260,14 @@ def advance_to(g, t_target, max_steps=1_000_000, regrid_every=0, crit=None, coun
 
 
 def propagate(g, cmes, *, t_inj, duration, sample=None, earth_lon0=math.pi, regrid_every=0, crit=None,
-              on_regrid=None, stop_after_arrival=None, progress=None):
+              on_regrid=None, stop_after_arrival=None, progress=None, max_wall_s=None):
     """Inject one cone CME per member at t_inj and record Earth time series
     every `sample` (default 10 min) for `duration`; returns RunResult.  With
     `stop_after_arrival` (code time), a member stops advancing once its shock
     has arrived and that much time has passed (its later samples repeat the
-    last state).  `progress` (a file) receives one line per simulated hour."""
+    last state).  `progress` (a file) receives one line per simulated hour.
+    With `max_wall_s`, the run ends early once that much wall clock has
+    passed, or once every member has stopped (the series are cut there)."""
     import time as _time
     sample = I.hours(1.0 / 6.0) if sample is None else sample
     nm = g.n_members
@@ -277,6 +297,10 @@ def propagate(g, cmes, *, t_inj, duration, sample=None, earth_lon0=math.pi, regr
         if progress is not None and int((times[k] - t_inj) / I.hours(1.0)) > int((times[k - 1] - t_inj) / I.hours(1.0)):
             print(f"t = {(times[k] - t_inj) / I.hours(1.0):.1f} h  wall {wall_at[k]:.1f} s  leaves {g.n_leaves(-1)}  "
                   f"held {int(np.sum(np.isfinite(t_hold)))}/{nm}", file=progress, flush=True)
+        all_held = stop_after_arrival is not None and bool(np.all(np.isfinite(t_hold)))
+        if (max_wall_s is not None and wall_at[k] > max_wall_s) or all_held:
+            times, series, bg, wall_at = times[:k + 1], series[:, :k + 1], bg[:, :k + 1], wall_at[:k + 1]
+            break
     wall = wall_at[-1]
     arr = [arrival_time(times, series[m, :, 1], bg[m, :, 1]) for m in range(nm)]
     wid = [shock_width(times, series[m, :, 1], a) for m, a in zip(range(nm), arr)]

@@ -79,21 +79,33 @@ def amr_report(g, res, wall_relax, t_inj, ups0=0.0):
 
 
 def run_cme(g, cmes, *, t_inj, hours_after=72.0, regrid_every=10, max_levels=None, learned=False,
-            sample_min=10.0, stop_hours_after_arrival=None, progress=None):
+            sample_min=10.0, stop_hours_after_arrival=None, progress=None, max_wall_s=None, records=None):
     """Inject one CME per member at t_inj and propagate for `hours_after`
     with regrids every `regrid_every` steps and Earth probes every
     `sample_min` minutes (a member stops `stop_hours_after_arrival` after its
-    shock arrival when given).  Returns the harness RunResult."""
+    shock arrival when given).  With a list `records`, every regrid appends
+    member 0's tree with the plain flags and the flags applied (the plain
+    estimator is evaluated on the same state as the learned pre-flags).
+    Returns the harness RunResult."""
+    from .icarus import FLAG_LEARNED, FLAG_PLAIN
     if max_levels is not None:
         for m, L in enumerate(max_levels):
             g.set_member_max_level(m, int(L))
     crit = dict(CRIT)
     if learned:
-        from .icarus import FLAG_LEARNED
         crit["mode"] = FLAG_LEARNED
+    hook = None
+    if records is not None:
+        def hook(gg, flags):
+            n0 = gg.n_leaves(0)
+            applied = np.array(flags, copy=True)
+            plain = gg.flag_refine(**dict(CRIT, mode=FLAG_PLAIN)) if learned else applied
+            records.append({"tree": gg.tree(0), "plain": np.array(plain[:n0]), "applied": applied[:n0]})
+            return applied
     stop = None if stop_hours_after_arrival is None else I.hours(stop_hours_after_arrival)
     return H.propagate(g, cmes, t_inj=t_inj, duration=I.hours(hours_after), sample=I.hours(sample_min / 60.0),
-                       regrid_every=regrid_every, crit=crit, stop_after_arrival=stop, progress=progress)
+                       regrid_every=regrid_every, crit=crit, stop_after_arrival=stop, progress=progress,
+                       max_wall_s=max_wall_s, on_regrid=hook)
 
 
 def step_profile(g, n_steps=20, crit=None, repeats=3):
@@ -201,14 +213,24 @@ def run_ladder_case(grid, kind=None, max_level=1, *, relax_days=10.0, hours_afte
     the shock's arrival."""
     tracer = kind in ("tracer", "combined")
     g = ladder_grid(grid, max_level=max_level, precision=precision, tracer=tracer, max_blocks=max_blocks)
+    # the floors of the CME's trailing near-vacuum are counted, not budgeted:
+    # on a small refined region they can be a large share of a step's cells
+    g.set_floor_budget(0.0)
     start_wind(g)
     t_inj, wall_relax = relax(g, relax_days)
     g.set_earth(0, 0.5 * math.pi, earth_lon0, t_inj, I.OMEGA_SYN)
     ups0 = float(np.sum(g.cell_updates()))
     crit = ladder_crit(kind) if max_level > 1 else None
-    res = H.propagate(g, [I.cme_config2(seed=0, earth_lon=earth_lon0)], t_inj=t_inj,
-                      duration=I.hours(hours_after), regrid_every=regrid_every if max_level > 1 else 0,
-                      crit=crit, earth_lon0=earth_lon0)
+    try:
+        res = H.propagate(g, [I.cme_config2(seed=0, earth_lon=earth_lon0)], t_inj=t_inj,
+                          duration=I.hours(hours_after), regrid_every=regrid_every if max_level > 1 else 0,
+                          crit=crit, earth_lon0=earth_lon0)
+    except IcarusError as e:
+        word, hits = g.status()
+        out = {"grid": grid, "max_level": max_level, "criterion": kind, "error": str(e), "status_word": word,
+               "floor_hits": int(hits), "leaves": g.n_leaves(-1)}
+        del g
+        return out
     rep = amr_report(g, res, wall_relax, t_inj, ups0)
     rep.update({"grid": grid, "cells": list(LADDER_GRIDS[grid][0]), "stretched": LADDER_GRIDS[grid][1],
                 "max_level": max_level, "criterion": kind, "time_to_arrival_s": res.wall_to(res.arrival[0]),
