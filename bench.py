@@ -82,7 +82,8 @@ def parse():
     p.add_argument("--relax-days", type=float, default=10.0)
     p.add_argument("--regrid-every", type=int, default=10)
     p.add_argument("--max-wall", type=float, default=None,
-                   help="ensemble: end the propagation after this many wall-clock seconds (reported)")
+                   help="ensemble / tt1au FP64 arm: end the propagation after this many wall-clock seconds "
+                        "(reported with the simulated hours reached)")
     p.add_argument("--rungs", default="low_str,middle_str,middle_eq,shock2,shock3,shock4,shock5,tracer2,tracer3,"
                    "combined2,combined3,combined4,combined5",
                    help="ladder: the single-level grids and <criterion><level> AMR runs on the Low stretched grid")
@@ -383,8 +384,10 @@ def run_tt1au_workload(args):
         # is the batch's wall clock / nm)
         recs = [] if nm == 1 and prec == FP32_MIXED else None
         res = WL.run_cme(g, [I.cme_config2(seed=0)] * nm, t_inj=t_inj, hours_after=args.hours,
-                         regrid_every=every, learned=learned, records=recs)
+                         regrid_every=every, learned=learned, records=recs,
+                         max_wall_s=args.max_wall if prec == FP64 else None)
         rep = WL.amr_report(g, res, wall_relax, t_inj, ups0)
+        rep["simulated_hours"] = float((res.times[-1] - t_inj) / I.hours(1.0))
         if recs:
             rep["missed_refinable_by_level"] = H.missed_by_level(recs, L, "applied")
             rep["regrid_every"] = every

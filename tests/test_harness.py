@@ -120,3 +120,17 @@ def test_threshold_calibration_and_bias_shift():
     # sigmoid(z + b') = 1/2 exactly where sigmoid(z + b) = 0.8
     z = math.log(0.8 / 0.2)
     assert abs(z + th[-1]) < 1e-6
+
+
+def test_missed_refinements_by_level():
+    """per level: the share of next-regrid refinements (below the finest
+    level) whose region the pre-flags did not mark"""
+    tk = _tree([[1, 0, 0, 0], [2, 2, 0, 0], [2, 3, 0, 0], [1, 2, 0, 0]])
+    recs = [{"tree": tk, "applied": np.array([1, 0, 1, 0], np.int8), "plain": np.zeros(4, np.int8)},
+            {"tree": tk, "applied": np.zeros(4, np.int8), "plain": np.array([1, 1, 1, 1], np.int8)}]
+    got = H.missed_by_level(recs, 3, "applied")
+    assert got == {1: 0.5, 2: 0.5}
+    # at the finest level flags cannot act: that level is not judged
+    assert H.missed_by_level(recs, 2, "applied") == {1: 0.5}
+    none = [dict(recs[0]), dict(recs[1], plain=np.zeros(4, np.int8))]
+    assert H.missed_by_level(none, 3, "applied") == {1: None, 2: None}
