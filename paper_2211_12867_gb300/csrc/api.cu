@@ -45,7 +45,7 @@ struct Layout {
       sides, rlist, ops, shell, staging, partial, probe_in, probe_out, mlp_par, mlp_feat, mlp_X, mlp_T, mlp_idx,
       mlp_act, mlp_xin;
   size_t staging_doubles = 0, table_doubles = 0;
-  int max_blocks = 0, nshell = 0;
+  int max_blocks = 0, nshell = 0;   // nshell: ghost cells of a padded block
   long long lmap_ints = 0;
   Region add(size_t b) {
     Region r;
@@ -250,6 +250,7 @@ struct icarus_ctx {
   bool graph_valid = false;
   bool poisoned = false;
   bool ghosts_fresh = false;   // ghosts of U filled for the current state and time
+  int nshell_face = 0;         // ghost cells outside the block in one direction (first in the shell list)
   std::vector<double> h_tstop;
   int kernels_per_step = 0;
   // learned pre-flagger
@@ -804,21 +805,28 @@ struct ProfScope {
   }
 };
 
-int enqueue_ghost(icarus_ctx *c, void *buf, double tfac) {
+// Ghost fill of buf at the member times (+ tfac dt).  faces_only: only the
+// ghost cells outside the block in exactly one direction -- enough for the
+// predictor stage, whose stencils are crosses and whose face fluxes take no
+// transverse halo; the corrector's cleaning takes div B on the ring around
+// the tile, which reaches edge ghosts, and the probe, the estimators and the
+// regrid get every ghost cell too.
+int enqueue_ghost(icarus_ctx *c, void *buf, double tfac, bool faces_only = false) {
   int n = 0;
+  const int nshell = faces_only ? c->nshell_face : c->lay.nshell;
   for (int L = 1; L <= c->max_level_present; L++) {
     if (c->lvl_count[L] == 0) continue;
     {
       ProfScope p(c, 1);
       ghost_neighbour_launch(c->kp, buf, c->prec, c->lvl_list + c->lvl_start[L], c->lvl_count[L], c->shell,
-                             c->lay.nshell, L, c->stream);
+                             nshell, L, c->stream);
     }
     n++;
     for (int dd = 0; dd < 3; dd++) {
       if (c->side_count[L][dd] == 0) continue;
       ProfScope p(c, 2);
       ghost_physical_launch(c->kp, buf, c->prec, c->sides + c->side_start[L][dd], c->side_count[L][dd], dd, L, tfac,
-                            c->stream);
+                            faces_only, c->stream);
       n++;
     }
   }
@@ -832,7 +840,7 @@ int enqueue_step(icarus_ctx *c) {
     dt_begin_launch(c->kp, c->tstop, c->stream);
   }
   n++;
-  n += enqueue_ghost(c, c->U, 0.0);
+  n += enqueue_ghost(c, c->U, 0.0, true);
   StageLaunch s1 = stage_cfg(c, 0);
   s1.Uin = c->U;
   s1.U0 = c->U;
@@ -1078,9 +1086,17 @@ icarus_status icarus_init_grid(const icarus_grid_desc *desc, icarus_ctx **out) {
     for (int i = 0; i < P0; i++)
       for (int j = 0; j < P1; j++)
         for (int k = 0; k < P2; k++) {
-          const bool in = i >= NGH && i < NGH + desc->block[0] && j >= NGH && j < NGH + desc->block[1] && k >= NGH &&
-                          k < NGH + desc->block[2];
-          if (!in) sh.push_back((i << 20) | (j << 10) | k);   // packed padded index
+          const int out = (i < NGH || i >= NGH + desc->block[0]) + (j < NGH || j >= NGH + desc->block[1]) +
+                          (k < NGH || k >= NGH + desc->block[2]);
+          if (out == 1) sh.push_back((i << 20) | (j << 10) | k);   // packed padded index
+        }
+    c->nshell_face = (int)sh.size();   // face ghosts first, then edges and corners
+    for (int i = 0; i < P0; i++)
+      for (int j = 0; j < P1; j++)
+        for (int k = 0; k < P2; k++) {
+          const int out = (i < NGH || i >= NGH + desc->block[0]) + (j < NGH || j >= NGH + desc->block[1]) +
+                          (k < NGH || k >= NGH + desc->block[2]);
+          if (out > 1) sh.push_back((i << 20) | (j << 10) | k);
         }
     if (cudaMemcpyAsync(c->shell, sh.data(), sizeof(int) * sh.size(), cudaMemcpyHostToDevice, c->stream) !=
             cudaSuccess ||

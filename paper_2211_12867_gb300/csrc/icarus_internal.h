@@ -139,7 +139,7 @@ int stage_max_ctas_per_sm(int precision, int tj, int tk, int tracer);
 void ghost_neighbour_launch(const KParams &kp, void *U, int precision, const int *list, int nlist,
                             const int *shell, int nshell, int level, cudaStream_t s);
 void ghost_physical_launch(const KParams &kp, void *U, int precision, const int2 *sides, int nsides,
-                           int dir, int level, double tshift_fac, cudaStream_t s);
+                           int dir, int level, double tshift_fac, bool faces_only, cudaStream_t s);
 void reflux_launch(const KParams &kp, void *U, const void *flux, int precision, const int *list, int nlist,
                    cudaStream_t s);
 void dt_begin_launch(const KParams &kp, const double *tstop, cudaStream_t s);

@@ -246,15 +246,17 @@ __device__ void inner_state(const KParams &kp, int member, int L, int J, int K, 
 }
 
 // physical boundary of direction `dir`; sides[n] = (slot, side)
+// faces: only the ghost cells inside the block in the two other directions
 template <typename real>
-__global__ void k_ghost_physical(const KParams kp, real *U, const int2 *sides, int dir, int L, double tfac) {
+__global__ void k_ghost_physical(const KParams kp, real *U, const int2 *sides, int dir, int L, double tfac,
+                                 int faces) {
   const int2 sd = sides[blockIdx.x];
   const int slot = sd.x, side = sd.y;
   const int da = dir == 0 ? 1 : 0, db = dir == 2 ? 1 : 2;
-  const int Pa = kp.P[da], Pb = kp.P[db];
+  const int Pa = faces ? kp.nb[da] : kp.P[da], Pb = faces ? kp.nb[db] : kp.P[db], off = faces ? NGH : 0;
   const int idx = blockIdx.y * blockDim.x + threadIdx.x;
   if (idx >= NGH * Pa * Pb) return;
-  const int gl = idx / (Pa * Pb), r = idx % (Pa * Pb), a = r / Pb, b = r % Pb;
+  const int gl = idx / (Pa * Pb), r = idx % (Pa * Pb), a = r / Pb + off, b = r % Pb + off;
   const int bc = side ? kp.bc_hi[dir] : kp.bc_lo[dir];
   const int nbd = kp.nb[dir];
   const int pg = side ? NGH + nbd + gl : NGH - 1 - gl;
@@ -486,15 +488,15 @@ void ghost_neighbour_launch(const KParams &kp, void *U, int precision, const int
 }
 
 void ghost_physical_launch(const KParams &kp, void *U, int precision, const int2 *sides, int nsides, int dir,
-                           int level, double tfac, cudaStream_t s) {
+                           int level, double tfac, bool faces_only, cudaStream_t s) {
   if (nsides <= 0) return;
   const int da = dir == 0 ? 1 : 0, db = dir == 2 ? 1 : 2;
-  const int n = NGH * kp.P[da] * kp.P[db];
+  const int n = faces_only ? NGH * kp.nb[da] * kp.nb[db] : NGH * kp.P[da] * kp.P[db];
   dim3 grid(nsides, (n + 127) / 128);
   if (precision)
-    k_ghost_physical<float><<<grid, 128, 0, s>>>(kp, (float *)U, sides, dir, level, tfac);
+    k_ghost_physical<float><<<grid, 128, 0, s>>>(kp, (float *)U, sides, dir, level, tfac, faces_only);
   else
-    k_ghost_physical<double><<<grid, 128, 0, s>>>(kp, (double *)U, sides, dir, level, tfac);
+    k_ghost_physical<double><<<grid, 128, 0, s>>>(kp, (double *)U, sides, dir, level, tfac, faces_only);
 }
 
 void reflux_launch(const KParams &kp, void *U, const void *flux, int precision, const int *list, int nlist,
