@@ -41,7 +41,7 @@ struct Region {
 
 struct Layout {
   size_t total = 0;
-  Region geo, tables, blk, blk_alt, U, Us, Ualt, flux, lmap, lmap_off, bmap, cme, earth, vbg, scal, flags, lists,
+  Region geo, tables, blk, blk_alt, nb27, U, Us, Ualt, flux, lmap, lmap_off, bmap, cme, earth, vbg, scal, flags, lists,
       sides, rlist, ops, shell, staging, partial, probe_in, probe_out, mlp_par, mlp_feat, mlp_X, mlp_T, mlp_idx,
       mlp_act, mlp_xin;
   size_t staging_doubles = 0, table_doubles = 0;
@@ -123,6 +123,7 @@ Layout make_layout(const icarus_grid_desc *d) {
   L.tables = L.add(L.table_doubles * (8 + 4));
   L.blk = L.add(mb * sizeof(DevBlock));
   L.blk_alt = L.add(amr ? mb * sizeof(DevBlock) : 0);
+  L.nb27 = L.add(mb * 27 * sizeof(int));
   const size_t nvs = NVAR + (d->tracer ? 1 : 0);   // variables stored per cell
   L.U = L.add(mb * nvs * pc * rs);
   L.Us = L.add(mb * nvs * pc * rs);
@@ -210,6 +211,7 @@ struct icarus_ctx {
   // device pointers
   Geometry *geo = nullptr;
   DevBlock *blk = nullptr, *blk_alt = nullptr;
+  int *nb27 = nullptr;
   void *U = nullptr, *Us = nullptr, *Ualt = nullptr, *flux = nullptr;
   int *lmap = nullptr;
   long long *lmap_off = nullptr;
@@ -251,6 +253,7 @@ struct icarus_ctx {
   bool poisoned = false;
   bool ghosts_fresh = false;   // ghosts of U filled for the current state and time
   int nshell_face = 0;         // ghost cells outside the block in one direction (first in the shell list)
+  bool direct_halo = true;     // stage kernels read same-level halos from the neighbours themselves
   std::vector<double> h_tstop;
   int kernels_per_step = 0;
   // learned pre-flagger
@@ -440,6 +443,7 @@ icarus_status upload_tree(icarus_ctx *c, DevBlock *blk_dst) {
   }
   if (c->nleaves > c->lay.max_blocks) return ICARUS_ERR_CAPACITY;
   c->hblk.assign(c->nleaves, DevBlock{});
+  std::vector<int> nb27((size_t)c->nleaves * 27, -1);
   std::vector<int> all(c->nleaves);
   std::vector<std::vector<int>> per_level(MAXLEV + 1);
   std::vector<std::vector<int2>> sd[3];
@@ -473,6 +477,15 @@ icarus_status upload_tree(icarus_ctx *c, DevBlock *blk_dst) {
         if (s == -2) finer = true;
       }
       if (finer) rl.push_back(slot);
+      // same-level leaves around the block (faces, edges, corners)
+      for (int dx = -1; dx <= 1; dx++)
+        for (int dy = -1; dy <= 1; dy++)
+          for (int dz = -1; dz <= 1; dz++) {
+            int b[3] = {l.ix[0] + dx, l.ix[1] + dy, l.ix[2] + dz};
+            if (!wrap_block(c, l.level, b)) continue;
+            const int s = region_state(c, M, l.level, b);
+            if (s >= 0) nb27[(size_t)slot * 27 + (dx + 1) * 9 + (dy + 1) * 3 + (dz + 1)] = c->mem_off[m] + s;
+          }
       all[slot] = slot;
       per_level[l.level].push_back(slot);
       c->max_level_present = std::max(c->max_level_present, l.level);
@@ -512,6 +525,7 @@ icarus_status upload_tree(icarus_ctx *c, DevBlock *blk_dst) {
   }
   cudaStream_t s = c->stream;
   CK(cudaMemcpyAsync(blk_dst, c->hblk.data(), sizeof(DevBlock) * c->nleaves, cudaMemcpyHostToDevice, s));
+  CK(cudaMemcpyAsync(c->nb27, nb27.data(), sizeof(int) * nb27.size(), cudaMemcpyHostToDevice, s));
   CK(cudaMemcpyAsync(c->lmap, lm.data(), sizeof(int) * lm.size(), cudaMemcpyHostToDevice, s));
   CK(cudaMemcpyAsync(c->lmap_off, off.data(), sizeof(long long) * off.size(), cudaMemcpyHostToDevice, s));
   CK(cudaMemcpyAsync(c->all_list, all.data(), sizeof(int) * all.size(), cudaMemcpyHostToDevice, s));
@@ -550,6 +564,7 @@ void fill_kp(icarus_ctx *c) {
   k.isl_beta = c->isl_beta;
   k.geo = c->geo;
   k.blk = c->blk;
+  k.nb27 = c->nb27;
   k.lmap = c->lmap;
   k.lmap_off = c->lmap_off;
   k.bmap = c->bmap;
@@ -811,7 +826,7 @@ struct ProfScope {
 // transverse halo; the corrector's cleaning takes div B on the ring around
 // the tile, which reaches edge ghosts, and the probe, the estimators and the
 // regrid get every ghost cell too.
-int enqueue_ghost(icarus_ctx *c, void *buf, double tfac, bool faces_only = false) {
+int enqueue_ghost(icarus_ctx *c, void *buf, double tfac, bool faces_only = false, bool skip_same = false) {
   int n = 0;
   const int nshell = faces_only ? c->nshell_face : c->lay.nshell;
   for (int L = 1; L <= c->max_level_present; L++) {
@@ -819,14 +834,14 @@ int enqueue_ghost(icarus_ctx *c, void *buf, double tfac, bool faces_only = false
     {
       ProfScope p(c, 1);
       ghost_neighbour_launch(c->kp, buf, c->prec, c->lvl_list + c->lvl_start[L], c->lvl_count[L], c->shell,
-                             nshell, L, c->stream);
+                             nshell, L, skip_same, c->stream);
     }
     n++;
     for (int dd = 0; dd < 3; dd++) {
       if (c->side_count[L][dd] == 0) continue;
       ProfScope p(c, 2);
       ghost_physical_launch(c->kp, buf, c->prec, c->sides + c->side_start[L][dd], c->side_count[L][dd], dd, L, tfac,
-                            faces_only, c->stream);
+                            faces_only, skip_same, c->stream);
       n++;
     }
   }
@@ -840,8 +855,11 @@ int enqueue_step(icarus_ctx *c) {
     dt_begin_launch(c->kp, c->tstop, c->stream);
   }
   n++;
-  n += enqueue_ghost(c, c->U, 0.0, true);
+  // the step's fills leave the ghost cells that same-level leaves hold to the
+  // stage kernels, which read them from those leaves
+  n += enqueue_ghost(c, c->U, 0.0, true, c->direct_halo);
   StageLaunch s1 = stage_cfg(c, 0);
+  s1.direct = c->direct_halo;
   s1.Uin = c->U;
   s1.U0 = c->U;
   s1.Uout = c->Us;
@@ -851,8 +869,9 @@ int enqueue_step(icarus_ctx *c) {
     stage_launch(c->kp, s1, c->prec, c->stream);
   }
   n++;
-  n += enqueue_ghost(c, c->Us, 0.5);
+  n += enqueue_ghost(c, c->Us, 0.5, false, c->direct_halo);
   StageLaunch s2 = stage_cfg(c, 1);
+  s2.direct = c->direct_halo;
   s2.Uin = c->Us;
   s2.U0 = c->U;
   s2.Uout = c->U;
@@ -1008,6 +1027,7 @@ icarus_status icarus_init_grid(const icarus_grid_desc *desc, icarus_ctx **out) {
   c->geo = at<Geometry>(c, lay.geo);
   c->blk = at<DevBlock>(c, lay.blk);
   c->blk_alt = lay.blk_alt.bytes ? at<DevBlock>(c, lay.blk_alt) : nullptr;
+  c->nb27 = at<int>(c, lay.nb27);
   c->U = c->arena + lay.U.off;
   c->Us = c->arena + lay.Us.off;
   c->Ualt = lay.Ualt.bytes ? c->arena + lay.Ualt.off : nullptr;

@@ -92,6 +92,9 @@ struct KParams {
   double gamma, omega, cd, p_floor, rho_floor;
   const Geometry *geo;
   const DevBlock *blk;
+  const int *nb27;             // [slot][27]: slot of the same-level leaf at block offset (dr, dth, dph) in
+                               // {-1,0,1}^3, index (dr+1)*9 + (dth+1)*3 + (dph+1); -1 if none (coarser,
+                               // finer or outside a non-periodic boundary)
   const int *lmap;             // level maps, concatenated
   const long long *lmap_off;   // [member * (MAXLEV+1) + L]
   const double *bmap;          // [member][8][n1][n2] inner boundary primitives
@@ -123,6 +126,7 @@ struct StageLaunch {
   int tiles_j, tiles_k, segs, seg_len;
   double dtfac;       // 0.5 (predictor) or 1 (corrector)
   int stage2;         // 1: cleaning, dt accumulation, reflux fluxes
+  int direct;         // 1: halo cells held by a same-level leaf are read from its interior
   int tile_j, tile_k; // tile shape
   int grid;           // CTAs (persistent loop)
 };
@@ -136,10 +140,13 @@ int stage_tile_supported(int precision, int tj, int tk, int tracer);
 int stage_max_ctas_per_sm(int precision, int tj, int tk, int tracer);
 
 // ghost fill
+// skip_same: ghost cells held by a same-level leaf are left unfilled (the
+// stage kernels read them from that leaf directly), and physical-boundary
+// copies and prolongation read such cells from the neighbour as well
 void ghost_neighbour_launch(const KParams &kp, void *U, int precision, const int *list, int nlist,
-                            const int *shell, int nshell, int level, cudaStream_t s);
+                            const int *shell, int nshell, int level, bool skip_same, cudaStream_t s);
 void ghost_physical_launch(const KParams &kp, void *U, int precision, const int2 *sides, int nsides,
-                           int dir, int level, double tshift_fac, bool faces_only, cudaStream_t s);
+                           int dir, int level, double tshift_fac, bool faces_only, bool skip_same, cudaStream_t s);
 void reflux_launch(const KParams &kp, void *U, const void *flux, int precision, const int *list, int nlist,
                    cudaStream_t s);
 void dt_begin_launch(const KParams &kp, const double *tstop, cudaStream_t s);

@@ -48,6 +48,24 @@ __device__ __forceinline__ size_t cell_index(const KParams &kp, int slot, int v,
   return ((((size_t)slot * kp.nvs + v) * kp.P[0] + p0) * kp.P[1] + p1) * kp.P[2] + p2;
 }
 
+// Variable v at padded index (p0, p1, p2) of leaf `slot`; with `direct`, a
+// cell of the ghost layer that a same-level leaf holds is read from that
+// leaf's interior (the ghost copy is not filled in the step's fills).
+template <typename real>
+__device__ __forceinline__ real fetch(const KParams &kp, const real *U, int slot, int v, int p0, int p1, int p2,
+                                      bool direct) {
+  if (direct) {
+    const int s0 = p0 < NGH ? -1 : (p0 >= NGH + kp.nb[0] ? 1 : 0);
+    const int s1 = p1 < NGH ? -1 : (p1 >= NGH + kp.nb[1] ? 1 : 0);
+    const int s2 = p2 < NGH ? -1 : (p2 >= NGH + kp.nb[2] ? 1 : 0);
+    if (s0 | s1 | s2) {
+      const int o = kp.nb27[(size_t)slot * 27 + (s0 + 1) * 9 + (s1 + 1) * 3 + (s2 + 1)];
+      if (o >= 0) return U[cell_index<real>(kp, o, v, p0 - s0 * kp.nb[0], p1 - s1 * kp.nb[1], p2 - s2 * kp.nb[2])];
+    }
+  }
+  return U[cell_index<real>(kp, slot, v, p0, p1, p2)];
+}
+
 // Conservative prolongation of coarse cell Ic (global at level Lc, held by
 // leaf slot cs) into the 2 x 2 x 2 ghost cells of leaf `slot` starting at
 // padded index p: child (i, j, k) = parent + MC slopes x offsets; if any
@@ -55,7 +73,8 @@ __device__ __forceinline__ size_t cell_index(const KParams &kp, int slot, int v,
 // value.  A first pass checks the eight children, a second writes them
 // (no per-child arrays held in registers).
 template <typename real>
-__device__ void prolong_into(const KParams &kp, real *U, int cs, int Lc, const int *Ic, int slot, const int *p) {
+__device__ void prolong_into(const KParams &kp, real *U, int cs, int Lc, const int *Ic, int slot, const int *p,
+                             bool direct) {
   const DevBlock C = kp.blk[cs];
   int pc[3];
 #pragma unroll
@@ -68,12 +87,12 @@ __device__ void prolong_into(const KParams &kp, real *U, int cs, int Lc, const i
   for (int v = 0; v < NVAR + 1; v++) {
     if (v >= nv) break;
     up[v] = U[cell_index<real>(kp, cs, v, pc[0], pc[1], pc[2])];
-    s[0][v] = mc_slope<real>(U[cell_index<real>(kp, cs, v, pc[0] - 1, pc[1], pc[2])], up[v],
-                             U[cell_index<real>(kp, cs, v, pc[0] + 1, pc[1], pc[2])]);
-    s[1][v] = mc_slope<real>(U[cell_index<real>(kp, cs, v, pc[0], pc[1] - 1, pc[2])], up[v],
-                             U[cell_index<real>(kp, cs, v, pc[0], pc[1] + 1, pc[2])]);
-    s[2][v] = mc_slope<real>(U[cell_index<real>(kp, cs, v, pc[0], pc[1], pc[2] - 1)], up[v],
-                             U[cell_index<real>(kp, cs, v, pc[0], pc[1], pc[2] + 1)]);
+    s[0][v] = mc_slope<real>(fetch(kp, U, cs, v, pc[0] - 1, pc[1], pc[2], direct), up[v],
+                             fetch(kp, U, cs, v, pc[0] + 1, pc[1], pc[2], direct));
+    s[1][v] = mc_slope<real>(fetch(kp, U, cs, v, pc[0], pc[1] - 1, pc[2], direct), up[v],
+                             fetch(kp, U, cs, v, pc[0], pc[1] + 1, pc[2], direct));
+    s[2][v] = mc_slope<real>(fetch(kp, U, cs, v, pc[0], pc[1], pc[2] - 1, direct), up[v],
+                             fetch(kp, U, cs, v, pc[0], pc[1], pc[2] + 1, direct));
   }
   const real *d0 = GeoSel<real>::dlt(kp.geo, Lc, 0), *d1 = GeoSel<real>::dlt(kp.geo, Lc, 1),
              *d2 = GeoSel<real>::dlt(kp.geo, Lc, 2);
@@ -147,7 +166,7 @@ __device__ bool restrict_in_block(const KParams &kp, const real *U, int member, 
 // ghost lies on (no divisions).
 template <typename real>
 __global__ void __launch_bounds__(256, sizeof(real) == 4 ? 4 : 2) k_ghost_neighbour(const KParams kp, real *U, const int *list, const int *shell, int nshell,
-                                  int L) {
+                                  int L, int skip_same) {
   const int s = blockIdx.y * blockDim.x + threadIdx.x;
   if (s >= nshell) return;
   const int slot = list[blockIdx.x];
@@ -172,6 +191,7 @@ __global__ void __launch_bounds__(256, sizeof(real) == 4 ? 4 : 2) k_ghost_neighb
   real val[NVAR + 1];
   const int nv = kp.nvs;
   const int o = lookup_block(kp, member, L, b);
+  if (o >= 0 && skip_same) return;   // the stage kernels read it from leaf o
   if (o >= 0) {
 #pragma unroll
     for (int v = 0; v < NVAR + 1; v++)
@@ -192,7 +212,7 @@ __global__ void __launch_bounds__(256, sizeof(real) == 4 ? 4 : 2) k_ghost_neighb
       atomicOr(kp.status, ST_NAN);
       return;
     }
-    prolong_into<real>(kp, U, cs, L - 1, Ic, slot, p);
+    prolong_into<real>(kp, U, cs, L - 1, Ic, slot, p, skip_same != 0);
     return;
   } else {
     if (!restrict_in_block<real>(kp, U, member, L, b, q, G, val)) {
@@ -249,7 +269,7 @@ __device__ void inner_state(const KParams &kp, int member, int L, int J, int K, 
 // faces: only the ghost cells inside the block in the two other directions
 template <typename real>
 __global__ void k_ghost_physical(const KParams kp, real *U, const int2 *sides, int dir, int L, double tfac,
-                                 int faces) {
+                                 int faces, int skip_same) {
   const int2 sd = sides[blockIdx.x];
   const int slot = sd.x, side = sd.y;
   const int da = dir == 0 ? 1 : 0, db = dir == 2 ? 1 : 2;
@@ -286,7 +306,7 @@ __global__ void k_ghost_physical(const KParams kp, real *U, const int2 *sides, i
 #pragma unroll
   for (int v = 0; v < NVAR + 1; v++) {
     if (v >= kp.nvs) break;
-    real x = U[cell_index<real>(kp, slot, v, s[0], s[1], s[2])];
+    real x = fetch(kp, U, slot, v, s[0], s[1], s[2], skip_same != 0);
     if (bc == 2 && (v == 1 + dir || v == 5 + dir)) x = -x;
     U[cell_index<real>(kp, slot, v, q[0], q[1], q[2])] = x;
   }
@@ -478,25 +498,25 @@ __global__ void k_dt_from_max(const KParams kp, double cfl) {
 }  // namespace
 
 void ghost_neighbour_launch(const KParams &kp, void *U, int precision, const int *list, int nlist, const int *shell,
-                            int nshell, int level, cudaStream_t s) {
+                            int nshell, int level, bool skip_same, cudaStream_t s) {
   if (nlist <= 0) return;
   dim3 grid(nlist, (nshell + 255) / 256);
   if (precision)
-    k_ghost_neighbour<float><<<grid, 256, 0, s>>>(kp, (float *)U, list, shell, nshell, level);
+    k_ghost_neighbour<float><<<grid, 256, 0, s>>>(kp, (float *)U, list, shell, nshell, level, skip_same);
   else
-    k_ghost_neighbour<double><<<grid, 256, 0, s>>>(kp, (double *)U, list, shell, nshell, level);
+    k_ghost_neighbour<double><<<grid, 256, 0, s>>>(kp, (double *)U, list, shell, nshell, level, skip_same);
 }
 
 void ghost_physical_launch(const KParams &kp, void *U, int precision, const int2 *sides, int nsides, int dir,
-                           int level, double tfac, bool faces_only, cudaStream_t s) {
+                           int level, double tfac, bool faces_only, bool skip_same, cudaStream_t s) {
   if (nsides <= 0) return;
   const int da = dir == 0 ? 1 : 0, db = dir == 2 ? 1 : 2;
   const int n = faces_only ? NGH * kp.nb[da] * kp.nb[db] : NGH * kp.P[da] * kp.P[db];
   dim3 grid(nsides, (n + 127) / 128);
   if (precision)
-    k_ghost_physical<float><<<grid, 128, 0, s>>>(kp, (float *)U, sides, dir, level, tfac, faces_only);
+    k_ghost_physical<float><<<grid, 128, 0, s>>>(kp, (float *)U, sides, dir, level, tfac, faces_only, skip_same);
   else
-    k_ghost_physical<double><<<grid, 128, 0, s>>>(kp, (double *)U, sides, dir, level, tfac, faces_only);
+    k_ghost_physical<double><<<grid, 128, 0, s>>>(kp, (double *)U, sides, dir, level, tfac, faces_only, skip_same);
 }
 
 void reflux_launch(const KParams &kp, void *U, const void *flux, int precision, const int *list, int nlist,

@@ -197,19 +197,35 @@ __global__ void __launch_bounds__(stage_threads(TJ, TK), stage_min_ctas(sizeof(r
     constexpr int NU = RP / 2;
     auto slotp = [&](int p) -> real * { return ring + ((p + 5) % 5) * NVAR * RP; };
     auto xslot = [&](int p) -> real * { return xring + ((p + 5) % 5) * RP; };
+    // Cells of the plane outside the block that a same-level leaf holds come
+    // straight from that leaf's interior (sl.direct: the step's ghost fills
+    // leave such ghost copies unfilled); the others from this block's ghost
+    // layer (coarser or finer neighbours, physical boundaries).
+    const int *nb27 = kp.nb27 + (size_t)slot * 27;
+    const real *Uall = reinterpret_cast<const real *>(sl.Uin);
     auto issue_plane = [&](int p) {
       real *dst = slotp(p);
-      const real *src = Uin + (size_t)(p + NGH) * plane;
+      const int sr = p < 0 ? -1 : (p >= nb0 ? 1 : 0);
       for (int u = NT - 1 - tid; u < NU; u += NT) {
 #pragma unroll
         for (int h = 0; h < 2; h++) {
           const int q = u + h * NU, jj = q / RK, kk = q - (q / RK) * RK;
           const int pj = j0 + jj, pk = k0 + kk;
           if (pj < P1 && pk < P2) {
+            const real *src = Uin + (size_t)(p + NGH) * plane + (size_t)pj * P2 + pk;
+            if (sl.direct) {
+              const int sj = pj < NGH ? -1 : (pj >= NGH + nb1 ? 1 : 0);
+              const int sk = pk < NGH ? -1 : (pk >= NGH + nb2 ? 1 : 0);
+              if (sr | sj | sk) {
+                const int o = nb27[(sr + 1) * 9 + (sj + 1) * 3 + (sk + 1)];
+                if (o >= 0)
+                  src = Uall + (size_t)o * bstride + (size_t)(p - sr * nb0 + NGH) * plane +
+                        (size_t)(pj - sj * nb1) * P2 + (pk - sk * nb2);
+              }
+            }
 #pragma unroll
-            for (int v = 0; v < NVAR; v++)
-              cp_async<sizeof(real)>(&el<real, RP>(dst, v, q), src + v * vstride + (size_t)pj * P2 + pk);
-            if (trc) cp_async<sizeof(real)>(xslot(p) + q, src + TRV * vstride + (size_t)pj * P2 + pk);
+            for (int v = 0; v < NVAR; v++) cp_async<sizeof(real)>(&el<real, RP>(dst, v, q), src + v * vstride);
+            if (trc) cp_async<sizeof(real)>(xslot(p) + q, src + TRV * vstride);
           }
         }
       }
