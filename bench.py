@@ -75,8 +75,9 @@ def parse():
     p.add_argument("--train-draws", type=int, default=3, help="tt1au: CME draws the pre-flagger is trained on")
     p.add_argument("--batch", type=int, default=8, help="tt1au: members of the batched learned arm")
     p.add_argument("--window-regrids", type=int, default=60, help="learned5: regrids after injection")
-    p.add_argument("--arms", default="fp32_learned,fp32_plain,fp64_plain",
-                   help="tt1au arms (fp32_learned, fp32_learned_batch, fp32_plain, fp64_plain)")
+    p.add_argument("--arms", default="fp32_learned,fp32_plain,fp64_plain,learned,plain",
+                   help="tt1au arms (fp32_learned, fp32_learned_batch, fp32_plain, fp64_plain); learned5 arms "
+                        "(learned, plain)")
     p.add_argument("--max-level", type=int, default=4)
     p.add_argument("--hours", type=float, default=72.0)
     p.add_argument("--relax-days", type=float, default=10.0)
@@ -421,24 +422,34 @@ def run_tt1au_workload(args):
 
 
 def run_learned5_workload(args):
-    """AMR level 5 with the learned pre-flagger: trained on the GPU from the
-    regrids of a level-4 run of another CME draw (labels: refinable flags one
-    regrid ahead), then applied at every regrid of a level-5 run of the
-    headline CME over a window after injection; reports the block counts,
-    the missed-flag rates of the learned and the plain pre-flags, and the
-    throughput."""
+    """AMR level 5 with the learned pre-flagger (the level-5 configuration):
+    trained on the GPU from the regrids of level-4 runs of other CME draws
+    (labels: refinable flags one regrid ahead), then applied at every regrid
+    (at twice the plain interval) of a level-5 run of the headline CME; with
+    --hours > 0 the run goes on to the shock's arrival at Earth (or
+    --max-wall) and a plain level-5 run with regrids every --regrid-every
+    steps is the reference.  Reports block counts, the missed refinements per
+    level of the learned and of the plain pre-flags, arrival, shock width and
+    peak speed of both, and the throughput."""
     import torch
     from paper_2211_12867_gb300 import harness as H
     from paper_2211_12867_gb300 import workloads as WL
     from paper_2211_12867_gb300.icarus import FP32_MIXED
     torch.cuda.set_device(0)
     every = 2 * args.regrid_every
-    g = WL.amr_grid(max_level=4, precision=FP32_MIXED, max_blocks=args.max_blocks)
-    WL.start_wind(g)
-    t_inj, _ = WL.relax(g, args.relax_days)
-    g.inject_cone_cme(0, t_start=t_inj, **I.cme_config2(seed=7))
-    recs = H.collect_regrids(g, n_regrids=args.train_regrids, regrid_every=every, crit=WL.CRIT)
-    X0, T0 = H.training_pairs(recs, max_level=4)
+    Xs, Ts = [], []
+    for seed in range(7, 7 + args.train_draws):
+        g = WL.amr_grid(max_level=4, precision=FP32_MIXED, max_blocks=args.max_blocks)
+        WL.start_wind(g)
+        t_inj, _ = WL.relax(g, args.relax_days)
+        g.inject_cone_cme(0, t_start=t_inj, **I.cme_config2(seed=seed))
+        recs = H.collect_regrids(g, n_regrids=args.train_regrids, regrid_every=every, crit=WL.CRIT)
+        x, t = H.training_pairs(recs, max_level=4)
+        Xs.append(x)
+        Ts.append(t)
+        if seed < 6 + args.train_draws:
+            del g
+    X0, T0 = np.concatenate(Xs), np.concatenate(Ts)
     X, T = H.rebalance(X0, T0, seed=2)
     g.mlp_set_params(I.mlp_init(5).astype(np.float32))
     g.mlp_dataset_clear()
@@ -447,21 +458,49 @@ def run_learned5_workload(args):
     thr, f1 = H.calibrate_threshold(g.mlp_predict(X0), T0)
     theta = H.shift_output_bias(g.mlp_get_params(), thr)
     del g
-    g = WL.amr_grid(max_level=5, precision=FP32_MIXED, max_blocks=args.max_blocks)
-    g.mlp_set_params(theta)
-    WL.start_wind(g)
-    t_inj, wall_relax = WL.relax(g, args.relax_days)
-    g.inject_cone_cme(0, t_start=t_inj, **I.cme_config2(seed=0))
-    ups0 = float(np.sum(g.cell_updates()))
-    rep = WL.run_learned_window(g, n_regrids=args.window_regrids, regrid_every=every, max_level=5)
-    ups = float(np.sum(g.cell_updates())) - ups0
-    t_end = g.step(0)[0]
-    print(json.dumps({"workload": "learned_amr264x36x96_L5", "train_pairs": int(len(T0)),
-                      "label_positive_fraction": float(T0.mean()), "threshold": thr, "train_f1": f1,
-                      "train_loss": [float(losses[0]), float(losses[-1])],
-                      "hours_after_injection": (t_end - t_inj) / I.hours(1.0), "cell_updates": ups,
-                      "cell_updates_per_s": ups / rep["wall_s"], "relax_wall_s": wall_relax,
-                      "status": g.status()[0], **rep}), flush=True)
+    head = {"workload": "learned_amr264x36x96_L5", "train_pairs": int(len(T0)), "train_draws": args.train_draws,
+            "label_positive_fraction": float(T0.mean()), "threshold": thr, "train_f1": f1,
+            "train_loss": [float(losses[0]), float(losses[-1])]}
+    if args.hours <= 0:
+        g = WL.amr_grid(max_level=5, precision=FP32_MIXED, max_blocks=args.max_blocks)
+        g.mlp_set_params(theta)
+        WL.start_wind(g)
+        t_inj, wall_relax = WL.relax(g, args.relax_days)
+        g.inject_cone_cme(0, t_start=t_inj, **I.cme_config2(seed=0))
+        ups0 = float(np.sum(g.cell_updates()))
+        rep = WL.run_learned_window(g, n_regrids=args.window_regrids, regrid_every=every, max_level=5)
+        ups = float(np.sum(g.cell_updates())) - ups0
+        t_end = g.step(0)[0]
+        print(json.dumps({**head, "hours_after_injection": (t_end - t_inj) / I.hours(1.0), "cell_updates": ups,
+                          "cell_updates_per_s": ups / rep["wall_s"], "relax_wall_s": wall_relax,
+                          "status": g.status()[0], **rep}), flush=True)
+        return 0
+    out = {}
+    for name, learned, ev in (("learned", True, every), ("plain", False, args.regrid_every)):
+        if name not in args.arms.split(","):
+            continue
+        g = WL.amr_grid(max_level=5, precision=FP32_MIXED, max_blocks=args.max_blocks)
+        if learned:
+            g.mlp_set_params(theta)
+        WL.start_wind(g)
+        t_inj, wall_relax = WL.relax(g, args.relax_days)
+        ups0 = float(np.sum(g.cell_updates()))
+        recs = []
+        res = WL.run_cme(g, [I.cme_config2(seed=0)], t_inj=t_inj, hours_after=args.hours, regrid_every=ev,
+                         learned=learned, records=recs, max_wall_s=args.max_wall, stop_hours_after_arrival=3.0)
+        rep = WL.amr_report(g, res, wall_relax, t_inj, ups0)
+        rep.update({"regrid_every": ev, "simulated_hours": float((res.times[-1] - t_inj) / I.hours(1.0)),
+                    "time_to_arrival_s": res.wall_to(res.arrival[0]),
+                    "missed_refinable_by_level": H.missed_by_level(recs, 5, "applied")})
+        out[name] = rep
+        print(json.dumps({"arm": name, **rep}), flush=True)
+        del g
+    diff = {}
+    if "learned" in out and "plain" in out:
+        for k in ("arrival_h", "peak_speed_kms", "shock_width_h"):
+            a, b = out["learned"][k][0], out["plain"][k][0]
+            diff[k] = None if (a is None or b is None) else a - b
+    print(json.dumps({**head, **out, "learned_minus_plain": diff}), flush=True)
     return 0
 
 
