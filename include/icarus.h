@@ -348,6 +348,13 @@ icarus_status icarus_set_floor_budget(icarus_ctx *ctx, double max_fraction);
  * than ~1e-4 of p); 0, 0 disables the islands.  No effect in FP64 mode. */
 icarus_status icarus_set_fp64_islands(icarus_ctx *ctx, double p_over_e, double beta);
 
+/* How the stage kernels get halo cells that a same-level leaf holds: 1 (the
+ * default) reads them from that leaf's interior, and the step's ghost fills
+ * skip them; 0 fills every ghost cell before each stage and reads the ghost
+ * layer.  Both give the same bits; the switch exists for tests and
+ * measurements. */
+icarus_status icarus_set_direct_halo(icarus_ctx *ctx, int enable);
+
 /* Capture one step of the launch sequence in a CUDA graph and replay it in
  * icarus_step (1) or launch kernels directly (0).  Default 1. */
 icarus_status icarus_use_graph(icarus_ctx *ctx, int enable);

@@ -1247,6 +1247,13 @@ icarus_status icarus_set_tile(icarus_ctx *c, int tj, int tk, int seg) {
   return ICARUS_OK;
 }
 
+icarus_status icarus_set_direct_halo(icarus_ctx *c, int enable) {
+  if (!c) return ICARUS_ERR_ARG;
+  c->direct_halo = enable != 0;
+  c->graph_valid = false;
+  return ICARUS_OK;
+}
+
 icarus_status icarus_use_graph(icarus_ctx *c, int enable) {
   if (!c) return ICARUS_ERR_ARG;
   c->use_graph = enable != 0;

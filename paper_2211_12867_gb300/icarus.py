@@ -39,7 +39,7 @@ EXPORTS = [
     "icarus_status_word", "icarus_set_tile", "icarus_use_graph", "icarus_kernels_per_step",
     "icarus_profile", "icarus_profile_read", "icarus_set_fp64_islands", "icarus_conservation_sums_static",
     "icarus_set_floor_budget", "icarus_get_padded", "icarus_set_earth", "icarus_get_tracer",
-    "icarus_set_tracer", "icarus_alu_peak",
+    "icarus_set_tracer", "icarus_alu_peak", "icarus_set_direct_halo",
     "icarus_mlp_set_params", "icarus_mlp_get_params", "icarus_mlp_features", "icarus_mlp_predict_leaves",
     "icarus_mlp_predict", "icarus_mlp_grad", "icarus_mlp_dataset_clear", "icarus_mlp_dataset_add",
     "icarus_mlp_train", "icarus_cell_updates", "icarus_save", "icarus_load", "icarus_destroy",
@@ -343,6 +343,14 @@ class Icarus:
 
     def set_tile(self, tile_theta=0, tile_phi=0, r_segment=0):
         _chk("icarus_set_tile", self.lib.icarus_set_tile(self.ctx, tile_theta, tile_phi, r_segment))
+
+    def set_direct_halo(self, enable=True):
+        """stage kernels read same-level halos from the neighbouring leaves (1)
+        or from ghost layers filled before every stage (0); same results"""
+        f = self.lib.icarus_set_direct_halo
+        f.restype = C.c_int
+        f.argtypes = [C.c_void_p, C.c_int]
+        _chk("icarus_set_direct_halo", f(self.ctx, int(bool(enable))))
 
     def use_graph(self, enable=True):
         _chk("icarus_use_graph", self.lib.icarus_use_graph(self.ctx, int(bool(enable))))
