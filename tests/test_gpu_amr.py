@@ -121,8 +121,8 @@ def test_flags_bit_exact_on_same_state():
 def test_direct_halo_reads_match_filled_ghosts(precision):
     """Reading same-level halos from the neighbouring leaves gives the same
     bits as filling every ghost cell before each stage: a stretched
-    three-level run with the cone CME, regrids and reflux, FP64 and FP32,
-    with and without the CME tracer."""
+    three-level run with the cone CME, regrids, reflux and the CME tracer,
+    in FP64 and FP32."""
     runs = []
     for direct in (True, False):
         g, o = make_pair(n=(48, 24, 48), nb=(12, 12, 12), max_level=3, max_blocks=4000, precision=precision,
