@@ -324,7 +324,9 @@ icarus_status icarus_get_dt(icarus_ctx *ctx, double *dt_out);
 icarus_status icarus_cell_updates(icarus_ctx *ctx, double *out);
 
 /* Sticky device status word: bit 0 NaN seen, bit 1 floor budget exceeded,
- * bit 2 bounded wait gave up; *floor_hits receives the floor counter. */
+ * bit 2 bounded wait gave up, bit 3 a ghost cell's neighbour was missing
+ * from the tree (balance broken; reported as ICARUS_ERR_NONPHYSICAL);
+ * *floor_hits receives the floor counter. */
 icarus_status icarus_status_word(icarus_ctx *ctx, uint32_t *word, uint64_t *floor_hits);
 
 /* Stage-kernel tile shape (theta x phi cells per CTA) and radial segment

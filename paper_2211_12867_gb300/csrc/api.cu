@@ -921,7 +921,7 @@ void permutation(std::vector<int> &p, int n, uint64_t &state) {
 
 // status of a status word read back from the device; poisons the context
 icarus_status status_of_word(icarus_ctx *c, unsigned int w) {
-  if (w & (ST_NAN | ST_FLOOR)) {
+  if (w & (ST_NAN | ST_FLOOR | ST_TREE)) {
     c->poisoned = true;
     return ICARUS_ERR_NONPHYSICAL;
   }
@@ -1753,6 +1753,14 @@ icarus_status icarus_regrid(icarus_ctx *c) {
     CK(cudaStreamSynchronize(c->stream));
   }
   std::swap(c->U, c->Ualt);
+  // the new trees must be balanced and cover the domain (a failure here is a
+  // defect of the balance step, reported rather than stepped through)
+  for (int m = 0; m < c->d.n_members; m++)
+    if (!tree_is_valid(c, c->mem[m])) {
+      fprintf(stderr, "libicarus: regrid produced an invalid tree for member %d\n", m);
+      c->poisoned = true;
+      return ICARUS_ERR_STATE;
+    }
   if ((st = upload_tree(c, c->blk)) != ICARUS_OK) return st;
   fill_kp(c);
   st = recompute_dt(c);

@@ -12,6 +12,7 @@
 #define ST_NAN 1u
 #define ST_FLOOR 2u
 #define ST_TIMEOUT 4u
+#define ST_TREE 8u       // a ghost cell's neighbour was not where the tree says (2:1 balance broken)
 
 // face-neighbour relation of a leaf face
 enum { NB_PHYS = 0, NB_SAME = 1, NB_COARSER = 2, NB_FINER = 3 };

@@ -209,14 +209,14 @@ __global__ void __launch_bounds__(256, sizeof(real) == 4 ? 4 : 2) k_ghost_neighb
     }
     const int cs = lookup_block(kp, member, L - 1, cb);
     if (cs < 0) {
-      atomicOr(kp.status, ST_NAN);
+      atomicOr(kp.status, ST_TREE);
       return;
     }
     prolong_into<real>(kp, U, cs, L - 1, Ic, slot, p, skip_same != 0);
     return;
   } else {
     if (!restrict_in_block<real>(kp, U, member, L, b, q, G, val)) {
-      atomicOr(kp.status, ST_NAN);
+      atomicOr(kp.status, ST_TREE);
       return;
     }
   }
@@ -356,7 +356,7 @@ __global__ void k_reflux(const KParams kp, real *U, const real *flux, const int 
           for (int e = 0; e < 3; e++) F[e] = wrap_dim(kp, L + 1, e, F[e], in);
           const int fsl = lookup(kp, B.member, L + 1, F);
           if (fsl < 0) {
-            atomicOr(kp.status, ST_NAN);
+            atomicOr(kp.status, ST_TREE);
             continue;
           }
           const DevBlock FB = kp.blk[fsl];
