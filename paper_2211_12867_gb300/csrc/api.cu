@@ -142,7 +142,7 @@ Layout make_layout(const icarus_grid_desc *d) {
   L.vbg = L.add((size_t)nm * d->n_cells[0] * d->n_cells[1] * d->n_cells[2] * sizeof(double));
   L.scal = L.add((size_t)nm * 7 * sizeof(double) + 64);
   L.flags = L.add(mb);
-  L.lists = L.add(2 * mb * sizeof(int));        // all-leaf list + per-level lists
+  L.lists = L.add(3 * mb * sizeof(int));        // all-leaf list + per-level lists + per-level coarse-fine lists
   L.sides = L.add(6 * mb * sizeof(int2));       // (slot, side) per level, per direction
   L.rlist = L.add(mb * sizeof(int));
   L.ops = L.add(amr ? mb * sizeof(MoveOp) : 0);
@@ -225,6 +225,7 @@ struct icarus_ctx {
   unsigned int *status = nullptr;
   signed char *flags = nullptr;
   int *all_list = nullptr, *lvl_list = nullptr, *rlist = nullptr, *shell = nullptr;
+  int *cf_list = nullptr;   // per level: leaves with a coarser or finer leaf among their 26 neighbours
   int2 *sides = nullptr;
   MoveOp *ops = nullptr;
   // host mirrors
@@ -233,6 +234,7 @@ struct icarus_ctx {
   std::vector<int> mem_off;                 // first slot of each member
   std::vector<DevBlock> hblk;
   int lvl_count[MAXLEV + 1] = {0}, lvl_start[MAXLEV + 1] = {0};
+  int cf_count[MAXLEV + 1] = {0}, cf_start[MAXLEV + 1] = {0};
   int side_count[MAXLEV + 1][3] = {{0}}, side_start[MAXLEV + 1][3] = {{0}};
   int nrlist = 0, max_level_present = 1;
   std::vector<signed char> hflags;
@@ -445,7 +447,7 @@ icarus_status upload_tree(icarus_ctx *c, DevBlock *blk_dst) {
   c->hblk.assign(c->nleaves, DevBlock{});
   std::vector<int> nb27((size_t)c->nleaves * 27, -1);
   std::vector<int> all(c->nleaves);
-  std::vector<std::vector<int>> per_level(MAXLEV + 1);
+  std::vector<std::vector<int>> per_level(MAXLEV + 1), cf_level(MAXLEV + 1);
   std::vector<std::vector<int2>> sd[3];
   for (int k = 0; k < 3; k++) sd[k].assign(MAXLEV + 1, std::vector<int2>());
   std::vector<int> rl;
@@ -478,6 +480,7 @@ icarus_status upload_tree(icarus_ctx *c, DevBlock *blk_dst) {
       }
       if (finer) rl.push_back(slot);
       // same-level leaves around the block (faces, edges, corners)
+      bool cf = false;
       for (int dx = -1; dx <= 1; dx++)
         for (int dy = -1; dy <= 1; dy++)
           for (int dz = -1; dz <= 1; dz++) {
@@ -485,7 +488,9 @@ icarus_status upload_tree(icarus_ctx *c, DevBlock *blk_dst) {
             if (!wrap_block(c, l.level, b)) continue;
             const int s = region_state(c, M, l.level, b);
             if (s >= 0) nb27[(size_t)slot * 27 + (dx + 1) * 9 + (dy + 1) * 3 + (dz + 1)] = c->mem_off[m] + s;
+            else cf = true;
           }
+      if (cf) cf_level[l.level].push_back(slot);
       all[slot] = slot;
       per_level[l.level].push_back(slot);
       c->max_level_present = std::max(c->max_level_present, l.level);
@@ -502,11 +507,14 @@ icarus_status upload_tree(icarus_ctx *c, DevBlock *blk_dst) {
       for (size_t q = 0; q < mp.size(); q++) lm[o + q] = mp[q] >= 0 ? mp[q] + c->mem_off[m] : mp[q];
       o += (long long)mp.size();
     }
-  std::vector<int> lv;
+  std::vector<int> lv, cfl;
   for (int L = 1; L <= MAXLEV; L++) {
     c->lvl_start[L] = (int)lv.size();
     c->lvl_count[L] = (int)per_level[L].size();
     lv.insert(lv.end(), per_level[L].begin(), per_level[L].end());
+    c->cf_start[L] = (int)cfl.size();
+    c->cf_count[L] = (int)cf_level[L].size();
+    cfl.insert(cfl.end(), cf_level[L].begin(), cf_level[L].end());
   }
   std::vector<int2> sv;
   for (int L = 1; L <= MAXLEV; L++)
@@ -530,6 +538,7 @@ icarus_status upload_tree(icarus_ctx *c, DevBlock *blk_dst) {
   CK(cudaMemcpyAsync(c->lmap_off, off.data(), sizeof(long long) * off.size(), cudaMemcpyHostToDevice, s));
   CK(cudaMemcpyAsync(c->all_list, all.data(), sizeof(int) * all.size(), cudaMemcpyHostToDevice, s));
   CK(cudaMemcpyAsync(c->lvl_list, lv.data(), sizeof(int) * lv.size(), cudaMemcpyHostToDevice, s));
+  if (!cfl.empty()) CK(cudaMemcpyAsync(c->cf_list, cfl.data(), sizeof(int) * cfl.size(), cudaMemcpyHostToDevice, s));
   if (!sv.empty()) CK(cudaMemcpyAsync(c->sides, sv.data(), sizeof(int2) * sv.size(), cudaMemcpyHostToDevice, s));
   if (!rl.empty()) CK(cudaMemcpyAsync(c->rlist, rl.data(), sizeof(int) * rl.size(), cudaMemcpyHostToDevice, s));
   // host buffers above are freed on return: wait for the copies
@@ -831,12 +840,15 @@ int enqueue_ghost(icarus_ctx *c, void *buf, double tfac, bool faces_only = false
   const int nshell = faces_only ? c->nshell_face : c->lay.nshell;
   for (int L = 1; L <= c->max_level_present; L++) {
     if (c->lvl_count[L] == 0) continue;
-    {
+    // skipping same-level ghosts leaves work only in leaves with a coarser or
+    // finer neighbour
+    const int *list = skip_same ? c->cf_list + c->cf_start[L] : c->lvl_list + c->lvl_start[L];
+    const int nlist = skip_same ? c->cf_count[L] : c->lvl_count[L];
+    if (nlist > 0) {
       ProfScope p(c, 1);
-      ghost_neighbour_launch(c->kp, buf, c->prec, c->lvl_list + c->lvl_start[L], c->lvl_count[L], c->shell,
-                             nshell, L, skip_same, c->stream);
+      ghost_neighbour_launch(c->kp, buf, c->prec, list, nlist, c->shell, nshell, L, skip_same, c->stream);
+      n++;
     }
-    n++;
     for (int dd = 0; dd < 3; dd++) {
       if (c->side_count[L][dd] == 0) continue;
       ProfScope p(c, 2);
@@ -1053,6 +1065,7 @@ icarus_status icarus_init_grid(const icarus_grid_desc *desc, icarus_ctx **out) {
   c->flags = at<signed char>(c, lay.flags);
   c->all_list = at<int>(c, lay.lists);
   c->lvl_list = c->all_list + lay.max_blocks;
+  c->cf_list = c->lvl_list + lay.max_blocks;
   c->sides = at<int2>(c, lay.sides);
   c->rlist = at<int>(c, lay.rlist);
   c->ops = lay.ops.bytes ? at<MoveOp>(c, lay.ops) : nullptr;
@@ -1265,7 +1278,9 @@ icarus_status icarus_kernels_per_step(icarus_ctx *c, int *n) {
   int k = 4 + (c->nrlist > 0 ? 1 : 0);  // dt begin, two stages, dt finalize, reflux
   for (int L = 1; L <= c->max_level_present; L++) {
     if (!c->lvl_count[L]) continue;
-    k += 2;                              // neighbour ghost pass, both fills
+    // neighbour ghost pass of both fills (with direct halo reads only over
+    // the leaves that have a coarser or finer neighbour)
+    if (c->direct_halo ? c->cf_count[L] : c->lvl_count[L]) k += 2;
     for (int d = 0; d < 3; d++)
       if (c->side_count[L][d]) k += 2;   // physical ghost pass, both fills
   }

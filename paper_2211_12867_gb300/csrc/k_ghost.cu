@@ -190,8 +190,15 @@ __global__ void __launch_bounds__(256, sizeof(real) == 4 ? 4 : 2) k_ghost_neighb
   }
   real val[NVAR + 1];
   const int nv = kp.nvs;
+  if (skip_same) {
+    // a cell a same-level leaf holds: the stage kernels read it from there
+    int sd[3];
+#pragma unroll
+    for (int d = 0; d < 3; d++) sd[d] = p[d] < NGH ? -1 : (p[d] >= NGH + kp.nb[d] ? 1 : 0);
+    if (kp.nb27[(size_t)slot * 27 + (sd[0] + 1) * 9 + (sd[1] + 1) * 3 + (sd[2] + 1)] >= 0) return;
+  }
   const int o = lookup_block(kp, member, L, b);
-  if (o >= 0 && skip_same) return;   // the stage kernels read it from leaf o
+  if (o >= 0 && skip_same) return;
   if (o >= 0) {
 #pragma unroll
     for (int v = 0; v < NVAR + 1; v++)
