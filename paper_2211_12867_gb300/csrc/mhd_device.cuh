@@ -41,8 +41,8 @@ template <> struct RT<float> {
 // Pressure from conserved variables.  In the mixed-precision mode the FP32
 // result is replaced by an FP64 recomputation from the same (FP32-stored)
 // conserved variables where the thermal energy is a small remainder of the
-// total: p < 0.05 e or plasma beta = p / (B^2/2) < 0.1.
-// thresholds of the FP64 pressure island (FP32 mode): p < pe * e or p < beta * B^2/2
+// total: p < pe * e or plasma beta = p / (B^2/2) < beta (settable; the
+// library's defaults are pe = 0.002 and beta = 0.1).
 struct Isl {
   float pe, beta;
 };

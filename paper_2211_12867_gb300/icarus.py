@@ -487,7 +487,7 @@ def alu_peak(kind, stream=None):
     return out.value
 
 
-def set_fp64_islands(g, p_over_e=0.05, beta=0.1):
+def set_fp64_islands(g, p_over_e=0.002, beta=0.1):
     """FP32 mode: FP64 pressure recovery where p < p_over_e * e or p < beta * B^2/2."""
     f = g.lib.icarus_set_fp64_islands
     f.restype = C.c_int
