@@ -81,6 +81,8 @@ def parse():
     p.add_argument("--max-level", type=int, default=4)
     p.add_argument("--hours", type=float, default=72.0)
     p.add_argument("--relax-days", type=float, default=10.0)
+    p.add_argument("--profile-range", action="store_true",
+                   help="amr: end with one step between cudaProfilerStart and cudaProfilerStop")
     p.add_argument("--regrid-every", type=int, default=10)
     p.add_argument("--max-wall", type=float, default=None,
                    help="ensemble / tt1au FP64 arm: end the propagation after this many wall-clock seconds "
@@ -287,7 +289,7 @@ def run_amr_workload(args):
     from paper_2211_12867_gb300.icarus import FP32_MIXED, FP64, set_fp64_islands
     torch.cuda.set_device(0)
     prec = FP32_MIXED if args.precision == "fp32" else FP64
-    g = WL.amr_grid(n_members=1, max_level=args.max_level, precision=prec)
+    g = WL.amr_grid(n_members=1, max_level=args.max_level, precision=prec, max_blocks=args.max_blocks)
     if prec == FP32_MIXED:
         set_fp64_islands(g, *(float(x) for x in args.islands.split(",")))
     WL.start_wind(g)
@@ -298,7 +300,16 @@ def run_amr_workload(args):
     rep = WL.amr_report(g, res, wall_relax, t_inj, ups0)
     line = {"workload": "amr264x36x96_L%d" % args.max_level, "precision": args.precision, **rep}
     print(json.dumps(line), flush=True)
-    print(json.dumps({"workload": line["workload"], "profile_at_end": WL.step_profile(g)}), flush=True)
+    lv = g.tree(0)[:, 0]
+    print(json.dumps({"workload": line["workload"], "profile_at_end": WL.step_profile(g),
+                      "leaves_by_level": [int((lv == q).sum()) for q in range(1, args.max_level + 1)]}), flush=True)
+    if args.profile_range:
+        # one more step inside cudaProfilerStart / Stop (ncu --profile-from-start off)
+        torch.cuda.synchronize()
+        torch.cuda.profiler.start()
+        g.step(1)
+        torch.cuda.synchronize()
+        torch.cuda.profiler.stop()
     return 0
 
 
@@ -328,6 +339,20 @@ def run_ensemble_workload(args):
     return 0
 
 
+class _Lines:
+    """A file-like sink that keeps the last line written (hourly progress)."""
+
+    def __init__(self):
+        self.last = None
+
+    def write(self, text):
+        if text.strip():
+            self.last = text.strip()
+
+    def flush(self):
+        pass
+
+
 def run_tt1au_workload(args):
     """Time to 1 AU: the plain FP64 single instance against the FP32 path with
     the learned pre-flagger (trained on a separate run's regrids) at a doubled
@@ -335,7 +360,7 @@ def run_tt1au_workload(args):
     import torch
     from paper_2211_12867_gb300 import harness as H
     from paper_2211_12867_gb300 import workloads as WL
-    from paper_2211_12867_gb300.icarus import FP32_MIXED, FP64
+    from paper_2211_12867_gb300.icarus import FP32_MIXED, FP64, IcarusError
     torch.cuda.set_device(0)
     L = args.max_level
     # training data: FP32 runs of other CME draws (seeds 7, 8, ...), labels
@@ -375,7 +400,9 @@ def run_tt1au_workload(args):
                                            ("fp64_plain", FP64, False, args.regrid_every, 1)):
         if (nm < 2 and name.startswith("fp32_learned_batch")) or name.split("_batch")[0] not in args.arms.split(","):
             continue
-        g = WL.amr_grid(n_members=nm, max_level=L, precision=prec, max_blocks=max(args.max_blocks, 15000 * nm))
+        # a level-4 member peaks near 47k leaves: the pool holds that per member
+        per_member = 50000 if L >= 4 else 15000
+        g = WL.amr_grid(n_members=nm, max_level=L, precision=prec, max_blocks=max(args.max_blocks, per_member * nm))
         if learned:
             g.mlp_set_params(theta)
         WL.start_wind(g)
@@ -384,9 +411,18 @@ def run_tt1au_workload(args):
         # a batch holds nm copies of the same CME run (the time per instance
         # is the batch's wall clock / nm)
         recs = [] if nm == 1 and prec == FP32_MIXED else None
-        res = WL.run_cme(g, [I.cme_config2(seed=0)] * nm, t_inj=t_inj, hours_after=args.hours,
-                         regrid_every=every, learned=learned, records=recs,
-                         max_wall_s=args.max_wall if prec == FP64 else None)
+        hourly = _Lines()
+        try:
+            res = WL.run_cme(g, [I.cme_config2(seed=0)] * nm, t_inj=t_inj, hours_after=args.hours,
+                             regrid_every=every, learned=learned, records=recs, progress=hourly,
+                             max_wall_s=args.max_wall if prec == FP64 else None)
+        except IcarusError as e:
+            word, hits = g.status()
+            out[name] = {"error": str(e), "status_word": word, "floor_hits": int(hits), "members": nm,
+                         "last_progress": hourly.last}
+            print(json.dumps({"arm": name, **out[name]}), flush=True)
+            del g
+            continue
         rep = WL.amr_report(g, res, wall_relax, t_inj, ups0)
         rep["simulated_hours"] = float((res.times[-1] - t_inj) / I.hours(1.0))
         if recs:
@@ -402,14 +438,18 @@ def run_tt1au_workload(args):
         out[name] = rep
         print(json.dumps({"arm": name, **{k: v for k, v in rep.items() if k != "series_at_earth"}}), flush=True)
         del g
-    arr = lambda k: out[k]["arrival_h"][0] if k in out else None
+    arr = lambda k: out[k].get("arrival_h", [None])[0] if k in out else None
     a32, a64 = arr("fp32_learned"), arr("fp64_plain")
     # FP32 against FP64 along the Earth probe series (both plain flags)
     serr = {}
-    if "fp32_plain" in out and "fp64_plain" in out:
+    if all("series_at_earth" in out.get(k, {}) for k in ("fp32_plain", "fp64_plain")):
         s32, s64 = out["fp32_plain"]["series_at_earth"], out["fp64_plain"]["series_at_earth"]
+        # both series sample every 10 minutes from the injection; an FP64 run
+        # cut by its wall-clock limit is compared over the hours it covers
+        nc = min(len(s32["t_h"]), len(s64["t_h"]))
+        serr["hours_compared"] = float(s64["t_h"][nc - 1])
         for key in ("vr_kms", "n"):
-            x, y = np.asarray(s32[key]), np.asarray(s64[key])
+            x, y = np.asarray(s32[key][:nc]), np.asarray(s64[key][:nc])
             serr[key + "_max_abs_diff"] = float(np.max(np.abs(x - y)))
             serr[key + "_max_rel_diff"] = float(np.max(np.abs(x - y)) / np.max(np.abs(y)))
     print(json.dumps({"workload": f"tt1au_amr264x36x96_L{L}", "train_pairs": int(len(T)),

@@ -1112,25 +1112,28 @@ icarus_status icarus_init_grid(const icarus_grid_desc *desc, icarus_ctx **out) {
       cudaMemsetAsync(c->arena + lay.Us.off, 0, lay.Us.bytes, c->stream) != cudaSuccess)
     return fail(ICARUS_ERR_CUDA);
   if ((st = build_geometry(c)) != ICARUS_OK) return fail(st);
-  // shell (ghost) cells of a padded block, in memory order
+  // shell (ghost) cells of a padded block: face ghosts first, then edges and
+  // corners; within each part the cells with even (p0, p1, p2) -- the first
+  // cells of the 2 x 2 x 2 groups a coarse neighbour's prolongation fills --
+  // come first, so that those threads share warps; memory order otherwise
   {
     std::vector<int> sh;
     const int P0 = desc->block[0] + 2 * NGH, P1 = desc->block[1] + 2 * NGH, P2 = desc->block[2] + 2 * NGH;
-    for (int i = 0; i < P0; i++)
-      for (int j = 0; j < P1; j++)
-        for (int k = 0; k < P2; k++) {
-          const int out = (i < NGH || i >= NGH + desc->block[0]) + (j < NGH || j >= NGH + desc->block[1]) +
-                          (k < NGH || k >= NGH + desc->block[2]);
-          if (out == 1) sh.push_back((i << 20) | (j << 10) | k);   // packed padded index
-        }
-    c->nshell_face = (int)sh.size();   // face ghosts first, then edges and corners
-    for (int i = 0; i < P0; i++)
-      for (int j = 0; j < P1; j++)
-        for (int k = 0; k < P2; k++) {
-          const int out = (i < NGH || i >= NGH + desc->block[0]) + (j < NGH || j >= NGH + desc->block[1]) +
-                          (k < NGH || k >= NGH + desc->block[2]);
-          if (out > 1) sh.push_back((i << 20) | (j << 10) | k);
-        }
+    auto add = [&](bool faces, bool leaders) {
+      for (int i = 0; i < P0; i++)
+        for (int j = 0; j < P1; j++)
+          for (int k = 0; k < P2; k++) {
+            const int out = (i < NGH || i >= NGH + desc->block[0]) + (j < NGH || j >= NGH + desc->block[1]) +
+                            (k < NGH || k >= NGH + desc->block[2]);
+            const bool lead = ((i | j | k) & 1) == 0;
+            if ((faces ? out == 1 : out > 1) && lead == leaders) sh.push_back((i << 20) | (j << 10) | k);
+          }
+    };
+    add(true, true);
+    add(true, false);
+    c->nshell_face = (int)sh.size();
+    add(false, true);
+    add(false, false);
     if (cudaMemcpyAsync(c->shell, sh.data(), sizeof(int) * sh.size(), cudaMemcpyHostToDevice, c->stream) !=
             cudaSuccess ||
         cudaStreamSynchronize(c->stream) != cudaSuccess)

@@ -43,76 +43,87 @@ __device__ __forceinline__ int lookup(const KParams &kp, int member, int L, cons
   return kp.lmap[off + ((long long)b0 * n1 + b1) * n2 + b2];
 }
 
-template <typename real>
 __device__ __forceinline__ size_t cell_index(const KParams &kp, int slot, int v, int p0, int p1, int p2) {
   return ((((size_t)slot * kp.nvs + v) * kp.P[0] + p0) * kp.P[1] + p1) * kp.P[2] + p2;
 }
 
-// Variable v at padded index (p0, p1, p2) of leaf `slot`; with `direct`, a
-// cell of the ghost layer that a same-level leaf holds is read from that
-// leaf's interior (the ghost copy is not filled in the step's fills).
-template <typename real>
-__device__ __forceinline__ real fetch(const KParams &kp, const real *U, int slot, int v, int p0, int p1, int p2,
-                                      bool direct) {
+// Index of variable 0 at padded index (p0, p1, p2) of leaf `slot` (variable
+// v lies v * P0 P1 P2 further on); with `direct`, a cell of the ghost layer
+// that a same-level leaf holds is located in that leaf's interior (the ghost
+// copy is not filled in the step's fills).
+__device__ __forceinline__ size_t locate(const KParams &kp, int slot, int p0, int p1, int p2, bool direct) {
   if (direct) {
     const int s0 = p0 < NGH ? -1 : (p0 >= NGH + kp.nb[0] ? 1 : 0);
     const int s1 = p1 < NGH ? -1 : (p1 >= NGH + kp.nb[1] ? 1 : 0);
     const int s2 = p2 < NGH ? -1 : (p2 >= NGH + kp.nb[2] ? 1 : 0);
     if (s0 | s1 | s2) {
       const int o = kp.nb27[(size_t)slot * 27 + (s0 + 1) * 9 + (s1 + 1) * 3 + (s2 + 1)];
-      if (o >= 0) return U[cell_index<real>(kp, o, v, p0 - s0 * kp.nb[0], p1 - s1 * kp.nb[1], p2 - s2 * kp.nb[2])];
+      if (o >= 0) return cell_index(kp, o, 0, p0 - s0 * kp.nb[0], p1 - s1 * kp.nb[1], p2 - s2 * kp.nb[2]);
     }
   }
-  return U[cell_index<real>(kp, slot, v, p0, p1, p2)];
+  return cell_index(kp, slot, 0, p0, p1, p2);
+}
+
+// variable v at padded index (p0, p1, p2) of leaf `slot` (see locate)
+template <typename real>
+__device__ __forceinline__ real fetch(const KParams &kp, const real *U, int slot, int v, int p0, int p1, int p2,
+                                      bool direct) {
+  return U[locate(kp, slot, p0, p1, p2, direct) + (size_t)v * kp.P[0] * kp.P[1] * kp.P[2]];
 }
 
 // Conservative prolongation of coarse cell Ic (global at level Lc, held by
 // leaf slot cs) into the 2 x 2 x 2 ghost cells of leaf `slot` starting at
 // padded index p: child (i, j, k) = parent + MC slopes x offsets; if any
 // child's density or pressure is not positive all eight take the parent
-// value.  A first pass checks the eight children, a second writes them
-// (no per-child arrays held in registers).
+// value.  The seven stencil cells are located once (all their loads are
+// independent); a first pass checks the eight children, a second writes them.
 template <typename real>
-__device__ void prolong_into(const KParams &kp, real *U, int cs, int Lc, const int *Ic, int slot, const int *p,
+__device__ __forceinline__ void prolong_into(const KParams &kp, real *U, int cs, int Lc, const int *Ic, int slot, const int *p,
                              bool direct) {
   const DevBlock C = kp.blk[cs];
   int pc[3];
 #pragma unroll
   for (int d = 0; d < 3; d++) pc[d] = Ic[d] - C.ix[d] * kp.nb[d] + NGH;
+  const size_t vs = (size_t)kp.P[0] * kp.P[1] * kp.P[2];
+  const size_t i0 = cell_index(kp, cs, 0, pc[0], pc[1], pc[2]);
+  const size_t im0 = locate(kp, cs, pc[0] - 1, pc[1], pc[2], direct), ip0 = locate(kp, cs, pc[0] + 1, pc[1], pc[2], direct);
+  const size_t im1 = locate(kp, cs, pc[0], pc[1] - 1, pc[2], direct), ip1 = locate(kp, cs, pc[0], pc[1] + 1, pc[2], direct);
+  const size_t im2 = locate(kp, cs, pc[0], pc[1], pc[2] - 1, direct), ip2 = locate(kp, cs, pc[0], pc[1], pc[2] + 1, direct);
   // the MHD variables and, when stored, the CME tracer (same slopes and
   // offsets; the positivity decision is the MHD variables')
   const int nv = kp.nvs;
   real up[NVAR + 1], s[3][NVAR + 1];
 #pragma unroll
   for (int v = 0; v < NVAR + 1; v++) {
-    if (v >= nv) break;
-    up[v] = U[cell_index<real>(kp, cs, v, pc[0], pc[1], pc[2])];
-    s[0][v] = mc_slope<real>(fetch(kp, U, cs, v, pc[0] - 1, pc[1], pc[2], direct), up[v],
-                             fetch(kp, U, cs, v, pc[0] + 1, pc[1], pc[2], direct));
-    s[1][v] = mc_slope<real>(fetch(kp, U, cs, v, pc[0], pc[1] - 1, pc[2], direct), up[v],
-                             fetch(kp, U, cs, v, pc[0], pc[1] + 1, pc[2], direct));
-    s[2][v] = mc_slope<real>(fetch(kp, U, cs, v, pc[0], pc[1], pc[2] - 1, direct), up[v],
-                             fetch(kp, U, cs, v, pc[0], pc[1], pc[2] + 1, direct));
+    if (v < nv) {
+      const size_t o = v * vs;
+      up[v] = U[i0 + o];
+      s[0][v] = mc_slope<real>(U[im0 + o], up[v], U[ip0 + o]);
+      s[1][v] = mc_slope<real>(U[im1 + o], up[v], U[ip1 + o]);
+      s[2][v] = mc_slope<real>(U[im2 + o], up[v], U[ip2 + o]);
+    }
   }
   const real *d0 = GeoSel<real>::dlt(kp.geo, Lc, 0), *d1 = GeoSel<real>::dlt(kp.geo, Lc, 1),
              *d2 = GeoSel<real>::dlt(kp.geo, Lc, 2);
   const real gamma = (real)kp.gamma;
+  const real a0 = d0[2 * Ic[0]], a1 = d0[2 * Ic[0] + 1], b0 = d1[2 * Ic[1]], b1 = d1[2 * Ic[1] + 1],
+             e0 = d2[2 * Ic[2]], e1 = d2[2 * Ic[2] + 1];
   bool ok = true;
   for (int c = 0; c < 8; c++) {
-    const real a = d0[2 * Ic[0] + ((c >> 2) & 1)], b = d1[2 * Ic[1] + ((c >> 1) & 1)], e = d2[2 * Ic[2] + (c & 1)];
+    const real a = (c & 4) ? a1 : a0, b = (c & 2) ? b1 : b0, e = (c & 1) ? e1 : e0;
     real u[NVAR];
 #pragma unroll
     for (int v = 0; v < NVAR; v++) u[v] = ((up[v] + s[0][v] * a) + s[1][v] * b) + s[2][v] * e;
     if (!(u[0] > real(0)) || !(pressure_of<real>(u, gamma, Isl{(float)kp.isl_pe, (float)kp.isl_beta}) > real(0))) ok = false;
   }
+  const size_t w0 = cell_index(kp, slot, 0, p[0], p[1], p[2]);
+  const int P1 = kp.P[1], P2 = kp.P[2];
   for (int c = 0; c < 8; c++) {
-    const real a = d0[2 * Ic[0] + ((c >> 2) & 1)], b = d1[2 * Ic[1] + ((c >> 1) & 1)], e = d2[2 * Ic[2] + (c & 1)];
-    const int q0 = p[0] + ((c >> 2) & 1), q1 = p[1] + ((c >> 1) & 1), q2 = p[2] + (c & 1);
+    const real a = (c & 4) ? a1 : a0, b = (c & 2) ? b1 : b0, e = (c & 1) ? e1 : e0;
+    const size_t wc = w0 + ((size_t)((c >> 2) & 1) * P1 + ((c >> 1) & 1)) * P2 + (c & 1);
 #pragma unroll
-    for (int v = 0; v < NVAR + 1; v++) {
-      if (v >= nv) break;
-      U[cell_index<real>(kp, slot, v, q0, q1, q2)] = ok ? ((up[v] + s[0][v] * a) + s[1][v] * b) + s[2][v] * e : up[v];
-    }
+    for (int v = 0; v < NVAR + 1; v++)
+      if (v < nv) U[wc + v * vs] = ok ? ((up[v] + s[0][v] * a) + s[1][v] * b) + s[2][v] * e : up[v];
   }
 }
 
@@ -125,37 +136,41 @@ __device__ __forceinline__ int lookup_block(const KParams &kp, int member, int L
 
 // volume-weighted mean of the 8 level-(L+1) cells under the level-L cell at
 // padded index q of the level-L block b (global cell G); same arithmetic and
-// order as the oracle's restriction
+// order as the oracle's restriction.  Block sizes are even, so the eight
+// children lie in one fine block: one lookup.
 template <typename real>
-__device__ bool restrict_in_block(const KParams &kp, const real *U, int member, int L, const int *b, const int *q,
+__device__ __forceinline__ bool restrict_in_block(const KParams &kp, const real *U, int member, int L, const int *b, const int *q,
                                   const int *G, real *out) {
   const LevelGeo<real> &F = GeoSel<real>::get(kp.geo, L + 1);
   const int nv = kp.nvs;
+  int fb[3], fq[3];
+#pragma unroll
+  for (int d = 0; d < 3; d++) {
+    const int l = 2 * (q[d] - NGH);   // first child, 0 .. 2 nb - 2 within the two fine blocks
+    const int hi = l >= kp.nb[d] ? 1 : 0;
+    fb[d] = 2 * b[d] + hi;
+    fq[d] = l - hi * kp.nb[d] + NGH;
+  }
+  const int fs = lookup_block(kp, member, L + 1, fb);
+  if (fs < 0) return false;
+  const size_t vs = (size_t)kp.P[0] * kp.P[1] * kp.P[2];
+  const size_t f0 = cell_index(kp, fs, 0, fq[0], fq[1], fq[2]);
+  const int P1 = kp.P[1], P2 = kp.P[2];
   real sum[NVAR + 1];
 #pragma unroll
   for (int v = 0; v < NVAR + 1; v++) sum[v] = real(0);
-  real vs = real(0);
+  real vsum = real(0);
   for (int c = 0; c < 8; c++) {
-    const int cb[3] = {(c >> 2) & 1, (c >> 1) & 1, c & 1};
-    int fb[3], fq[3];
-#pragma unroll
-    for (int d = 0; d < 3; d++) {
-      const int l = 2 * (q[d] - NGH) + cb[d];   // 0 .. 2 nb - 1 within the two fine blocks
-      const int hi = l >= kp.nb[d] ? 1 : 0;
-      fb[d] = 2 * b[d] + hi;
-      fq[d] = l - hi * kp.nb[d] + NGH;
-    }
-    const int fs = lookup_block(kp, member, L + 1, fb);
-    if (fs < 0) return false;
-    const int f0 = 2 * G[0] + cb[0], f1 = 2 * G[1] + cb[1];
-    const real V = F.dr3[f0 + NGH] * F.dcos[f1 + NGH] * F.dphi;
+    const int c0 = (c >> 2) & 1, c1 = (c >> 1) & 1, c2 = c & 1;
+    const real V = F.dr3[2 * G[0] + c0 + NGH] * F.dcos[2 * G[1] + c1 + NGH] * F.dphi;
+    const size_t o = f0 + ((size_t)c0 * P1 + c1) * P2 + c2;
 #pragma unroll
     for (int v = 0; v < NVAR + 1; v++)
-      if (v < nv) sum[v] += V * U[cell_index<real>(kp, fs, v, fq[0], fq[1], fq[2])];
-    vs += V;
+      if (v < nv) sum[v] += V * U[o + v * vs];
+    vsum += V;
   }
 #pragma unroll
-  for (int v = 0; v < NVAR + 1; v++) out[v] = sum[v] / vs;
+  for (int v = 0; v < NVAR + 1; v++) out[v] = sum[v] / vsum;
   return true;
 }
 
@@ -202,7 +217,7 @@ __global__ void __launch_bounds__(256, sizeof(real) == 4 ? 4 : 2) k_ghost_neighb
   if (o >= 0) {
 #pragma unroll
     for (int v = 0; v < NVAR + 1; v++)
-      if (v < nv) val[v] = U[cell_index<real>(kp, o, v, q[0], q[1], q[2])];
+      if (v < nv) val[v] = U[cell_index(kp, o, v, q[0], q[1], q[2])];
   } else if (o == -1) {
     // A coarse cell covers a 2 x 2 x 2 group of ghost cells (blocks start at
     // even global indices and there are two ghost layers): the group's
@@ -229,7 +244,7 @@ __global__ void __launch_bounds__(256, sizeof(real) == 4 ? 4 : 2) k_ghost_neighb
   }
 #pragma unroll
   for (int v = 0; v < NVAR + 1; v++)
-    if (v < nv) U[cell_index<real>(kp, slot, v, p[0], p[1], p[2])] = val[v];
+    if (v < nv) U[cell_index(kp, slot, v, p[0], p[1], p[2])] = val[v];
 }
 
 // inner boundary state (FP64): map of the containing base cell, cone CME
@@ -306,7 +321,7 @@ __global__ void k_ghost_physical(const KParams kp, real *U, const int2 *sides, i
     inner_state(kp, B.member, L, J, K, t, u);
 #pragma unroll
     for (int v = 0; v < NVAR + 1; v++)
-      if (v < kp.nvs) U[cell_index<real>(kp, slot, v, q[0], q[1], q[2])] = (real)u[v];
+      if (v < kp.nvs) U[cell_index(kp, slot, v, q[0], q[1], q[2])] = (real)u[v];
     return;
   }
   s[dir] = bc == 2 ? pm : pn;
@@ -315,7 +330,7 @@ __global__ void k_ghost_physical(const KParams kp, real *U, const int2 *sides, i
     if (v >= kp.nvs) break;
     real x = fetch(kp, U, slot, v, s[0], s[1], s[2], skip_same != 0);
     if (bc == 2 && (v == 1 + dir || v == 5 + dir)) x = -x;
-    U[cell_index<real>(kp, slot, v, q[0], q[1], q[2])] = x;
+    U[cell_index(kp, slot, v, q[0], q[1], q[2])] = x;
   }
 }
 
@@ -382,7 +397,7 @@ __global__ void k_reflux(const KParams kp, real *U, const real *flux, const int 
       const real sg = hi ? real(-1) : real(1);
 #pragma unroll
       for (int v = 0; v < NVAR; v++) {
-        const size_t ci = cell_index<real>(kp, slot, v, q[0], q[1], q[2]);
+        const size_t ci = cell_index(kp, slot, v, q[0], q[1], q[2]);
         U[ci] += sg * dt / V * (fs[v] - own[(size_t)v * fc[d] + t]);
       }
     }
@@ -404,10 +419,10 @@ __global__ void k_reflux(const KParams kp, real *U, const real *flux, const int 
       q[d2] = NGH + t2;
       real u[NVAR];
 #pragma unroll
-      for (int v = 0; v < NVAR; v++) u[v] = U[cell_index<real>(kp, slot, v, q[0], q[1], q[2])];
+      for (int v = 0; v < NVAR; v++) u[v] = U[cell_index(kp, slot, v, q[0], q[1], q[2])];
       hits += apply_floors<real>(u, gamma, pfl, rfl, Isl{(float)kp.isl_pe, (float)kp.isl_beta});
 #pragma unroll
-      for (int v = 0; v < NVAR; v++) U[cell_index<real>(kp, slot, v, q[0], q[1], q[2])] = u[v];
+      for (int v = 0; v < NVAR; v++) U[cell_index(kp, slot, v, q[0], q[1], q[2])] = u[v];
       real w[NVAR];
       cons2prim_speed<real>(u, w, gamma, pfl);
       const int I = B.ix[0] * nb0 + q[0] - NGH + NGH, J = B.ix[1] * nb1 + q[1] - NGH + NGH;
@@ -477,7 +492,7 @@ __global__ void k_dt_full(const KParams kp, const real *U) {
     const int k = c % kp.nb[2], j = (c / kp.nb[2]) % kp.nb[1], i = c / (kp.nb[2] * kp.nb[1]);
     real u[NVAR], w[NVAR];
 #pragma unroll
-    for (int v = 0; v < NVAR; v++) u[v] = U[cell_index<real>(kp, slot, v, i + NGH, j + NGH, k + NGH)];
+    for (int v = 0; v < NVAR; v++) u[v] = U[cell_index(kp, slot, v, i + NGH, j + NGH, k + NGH)];
     cons2prim_speed<real>(u, w, gamma, pfl);
     const int I = B.ix[0] * kp.nb[0] + i + NGH, J = B.ix[1] * kp.nb[1] + j + NGH;
     real dx0 = G.dr[I], dx1 = G.dth[J], dx2 = G.dphi;

@@ -39,10 +39,10 @@ struct StageSmem {
                                    NVAR * ((tj * tk + 31) / 32 * 32) + geo(tj, tk) +
                                    (tracer ? 5 * (tj + 4) * (tk + 4) : 0));
   }
-  // geometry of one work item: 4 plane arrays and the faces in r, 5 row
-  // arrays and the faces in theta, the phi centres
+  // geometry of one work item: 6 plane arrays and the faces in r, 6 row
+  // arrays and the faces in theta, 1 column array
   static constexpr int geo(int tj, int tk) {
-    return 4 * (STAGE_SEG_MAX + 4) + (STAGE_SEG_MAX + 5) + 5 * (tj + 4) + (tj + 5) + (tk + 4);
+    return 6 * (STAGE_SEG_MAX + 4) + (STAGE_SEG_MAX + 5) + 6 * (tj + 4) + (tj + 5) + (tk + 4);
   }
 };
 
@@ -134,12 +134,16 @@ __global__ void __launch_bounds__(stage_threads(TJ, TK), stage_min_ctas(sizeof(r
   // geometry of the work item (plane arrays from plane ib-2, row arrays from
   // row -2 of the tile, phi centres from column -2)
   constexpr int NRP = STAGE_SEG_MAX + 4, NJ = TJ + 4;
-  real *s_rc = u0s + NVAR * NT, *s_dr = s_rc + NRP, *s_dr2 = s_dr + NRP, *s_dr3 = s_dr2 + NRP;
+  real *s_rc = u0s + NVAR * NT, *s_dr2 = s_rc + NRP, *s_dr3 = s_dr2 + NRP;
   real *s_r2f = s_dr3 + NRP;                                  // STAGE_SEG_MAX + 5 faces
-  real *s_tc = s_r2f + NRP + 1, *s_st = s_tc + NJ, *s_ct = s_st + NJ, *s_dcos = s_ct + NJ, *s_dth = s_dcos + NJ;
+  // reciprocal centre spacings over two cells (theta rows, phi columns, r
+  // planes), reciprocal widths and radii: the divergence and the cleaning
+  // gradient take these per row, column or plane
+  real *s_itc2 = s_r2f + NRP + 1, *s_st = s_itc2 + NJ, *s_ct = s_st + NJ, *s_dcos = s_ct + NJ, *s_dth = s_dcos + NJ;
   real *s_sinf = s_dth + NJ;                                  // TJ + 5 faces
-  real *s_pc = s_sinf + NJ + 1;                               // TK + 4
-  real *xring = s_pc + TK + 4;                                // tracer X, 5 planes (if stored)
+  real *s_ipc2 = s_sinf + NJ + 1;                             // TK + 4
+  real *s_ird2 = s_ipc2 + TK + 4, *s_idr = s_ird2 + NRP, *s_irc = s_idr + NRP, *s_idth = s_irc + NRP;
+  real *xring = s_idth + NJ;                                  // tracer X, 5 planes (if stored)
   const bool trc = kp.nvs > NVAR;
 
   const int tid = threadIdx.x, jl = tid / TK, kl = tid % TK;
@@ -296,17 +300,15 @@ __global__ void __launch_bounds__(stage_threads(TJ, TK), stage_min_ctas(sizeof(r
         const real brm = el<real, RP>(pm, 5, o), brp = el<real, RP>(pp, 5, o);
         const real btm = el<real, RP>(pc, 6, o - RK), btp = el<real, RP>(pc, 6, o + RK);
         const real bpm = el<real, RP>(pc, 7, o - 1), bpp = el<real, RP>(pc, 7, o + 1);
-        const real tcm = s_tc[dj + 1], tcp = s_tc[dj + 3];
-        const real pcm = s_pc[dk + 1], pcp = s_pc[dk + 3];
+        const real itc2 = s_itc2[dj + 2], ipc2 = s_ipc2[dk + 2];
         real div;
         if (spherical) {
           const real stc = s_st[dj + 2];
           const real sm = s_st[dj + 1], sp = s_st[dj + 3];
           const real irs = RT<real>::rcp_(rcc * stc);
-          div = (wp * brp - wm * brm) * fr + (sp * btp - sm * btm) * irs * RT<real>::rcp_(tcp - tcm) +
-                (bpp - bpm) * irs * RT<real>::rcp_(pcp - pcm);
+          div = (wp * brp - wm * brm) * fr + (sp * btp - sm * btm) * irs * itc2 + (bpp - bpm) * irs * ipc2;
         } else {
-          div = (brp - brm) * fr + (btp - btm) * RT<real>::rcp_(tcp - tcm) + (bpp - bpm) * RT<real>::rcp_(pcp - pcm);
+          div = (brp - brm) * fr + (btp - btm) * itc2 + (bpp - bpm) * ipc2;
         }
         dst[q] = div;
       }
@@ -319,23 +321,27 @@ __global__ void __launch_bounds__(stage_threads(TJ, TK), stage_min_ctas(sizeof(r
       const int npl = ie - ib + 4, ir0 = I0 + ib - 2 + NGH;
       for (int q = tid; q < npl; q += NT) {
         s_rc[q] = G.rc[ir0 + q];
-        s_dr[q] = G.dr[ir0 + q];
         s_dr2[q] = G.dr2[ir0 + q];
         s_dr3[q] = G.dr3[ir0 + q];
+        s_idr[q] = RT<real>::rcp_(G.dr[ir0 + q]);
+        s_irc[q] = RT<real>::rcp_(G.rc[ir0 + q]);
+        if (q >= 1 && q + 1 < npl) s_ird2[q] = RT<real>::rcp_(G.rc[ir0 + q + 1] - G.rc[ir0 + q - 1]);
       }
       for (int q = tid; q <= npl; q += NT) s_r2f[q] = G.r2f[ir0 + q];
       const int jr0 = J0 - 2 + NGH;
       for (int q = tid; q < nvj + 4; q += NT) {
-        s_tc[q] = G.tc[jr0 + q];
+        if (q >= 1 && q + 1 < nvj + 4) s_itc2[q] = RT<real>::rcp_(G.tc[jr0 + q + 1] - G.tc[jr0 + q - 1]);
         s_st[q] = G.sintc[jr0 + q];
         s_ct[q] = G.costc[jr0 + q];
         s_dcos[q] = G.dcos[jr0 + q];
         s_dth[q] = G.dth[jr0 + q];
+        s_idth[q] = RT<real>::rcp_(G.dth[jr0 + q]);
       }
       for (int q = tid; q <= nvj + 4; q += NT) s_sinf[q] = G.sinf[jr0 + q];
-      for (int q = tid; q < nvk + 4; q += NT) s_pc[q] = G.pc[K0 - 2 + NGH + q];
+      const int kr0 = K0 - 2 + NGH;
+      for (int q = 1 + tid; q + 1 < nvk + 4; q += NT) s_ipc2[q] = RT<real>::rcp_(G.pc[kr0 + q + 1] - G.pc[kr0 + q - 1]);
     }
-    const real dphi = G.dphi;
+    const real dphi = G.dphi, idphi = RT<real>::rcp_(dphi);
 
     // ---- prologue: planes ib-2 .. ib+2 converted, r flux at face ib ----
     for (int p = ib - 2; p <= ib + 2; p++) issue_plane(p);
@@ -472,25 +478,21 @@ __global__ void __launch_bounds__(stage_threads(TJ, TK), stage_min_ctas(sizeof(r
         if (S2 && Cd > real(0)) {
           const real *dm = dring + ((i - 1) & 3) * DP, *dc = dring + (i & 3) * DP, *dp = dring + ((i + 1) & 3) * DP;
           const int q = (jl + 1) * DK + (kl + 1);
-          const real rcm = s_rc[pr - 1], rcc = s_rc[pr], rcp = s_rc[pr + 1];
-          const real tcm = s_tc[jr - 1], tcp = s_tc[jr + 1];
-          const real pcm = s_pc[kl + 1], pcp = s_pc[kl + 3];
-          const real dr = s_dr[pr], dth = s_dth[jr];
+          const real ird2 = s_ird2[pr], itc2 = s_itc2[jr], ipc2 = s_ipc2[kl + 2];
+          const real idr = s_idr[pr], idth = s_idth[jr];
           real gr_, gt_, gp_, h2inv;
           if (spherical) {
-            const real st = s_st[jr];
-            const real irc = RT<real>::rcp_(rcc), irs = RT<real>::rcp_(rcc * st);
-            gr_ = (dp[q] - dm[q]) * RT<real>::rcp_(rcp - rcm);
-            gt_ = (dc[q + DK] - dc[q - DK]) * irc * RT<real>::rcp_(tcp - tcm);
-            gp_ = (dc[q + 1] - dc[q - 1]) * irs * RT<real>::rcp_(pcp - pcm);
-            const real idr = RT<real>::rcp_(dr), ixt = irc * RT<real>::rcp_(dth), ixp = irs * RT<real>::rcp_(dphi);
+            const real irc = s_irc[pr], irs = RT<real>::rcp_(s_rc[pr] * s_st[jr]);
+            gr_ = (dp[q] - dm[q]) * ird2;
+            gt_ = (dc[q + DK] - dc[q - DK]) * irc * itc2;
+            gp_ = (dc[q + 1] - dc[q - 1]) * irs * ipc2;
+            const real ixt = irc * idth, ixp = irs * idphi;
             h2inv = idr * idr + ixt * ixt + ixp * ixp;
           } else {
-            gr_ = (dp[q] - dm[q]) * RT<real>::rcp_(rcp - rcm);
-            gt_ = (dc[q + DK] - dc[q - DK]) * RT<real>::rcp_(tcp - tcm);
-            gp_ = (dc[q + 1] - dc[q - 1]) * RT<real>::rcp_(pcp - pcm);
-            const real idr = RT<real>::rcp_(dr), idt = RT<real>::rcp_(dth), idp = RT<real>::rcp_(dphi);
-            h2inv = idr * idr + idt * idt + idp * idp;
+            gr_ = (dp[q] - dm[q]) * ird2;
+            gt_ = (dc[q + DK] - dc[q - DK]) * itc2;
+            gp_ = (dc[q + 1] - dc[q - 1]) * ipc2;
+            h2inv = idr * idr + idth * idth + idphi * idphi;
           }
           const real f = Cd * RT<real>::rcp_(h2inv);
           const real dB0 = f * gr_, dB1 = f * gt_, dB2 = f * gp_;
@@ -532,12 +534,12 @@ __global__ void __launch_bounds__(stage_threads(TJ, TK), stage_min_ctas(sizeof(r
           if (!skip) {
             real wn[NVAR];
             cons2prim_speed<real>(un, wn, gamma, pfl);
-            real dx0 = s_dr[pr], dx1 = s_dth[jr], dx2 = dphi;
+            real dx1 = s_dth[jr], dx2 = dphi;
             if (spherical) {
               dx1 *= s_rc[pr];
               dx2 *= s_rc[pr] * s_st[jr];
             }
-            const real s = (RT<real>::abs_(wn[1]) + fast_speed<real, 0>(wn, gamma)) * RT<real>::rcp_(dx0) +
+            const real s = (RT<real>::abs_(wn[1]) + fast_speed<real, 0>(wn, gamma)) * s_idr[pr] +
                            (RT<real>::abs_(wn[2]) + fast_speed<real, 1>(wn, gamma)) * RT<real>::rcp_(dx1) +
                            (RT<real>::abs_(wn[3]) + fast_speed<real, 2>(wn, gamma)) * RT<real>::rcp_(dx2);
             inv_acc = RT<real>::max_(inv_acc, s);
