@@ -42,7 +42,7 @@ struct Region {
 struct Layout {
   size_t total = 0;
   Region geo, tables, blk, blk_alt, nb27, U, Us, Ualt, flux, lmap, lmap_off, bmap, cme, earth, vbg, scal, flags, lists,
-      sides, rlist, ops, shell, staging, partial, probe_in, probe_out, mlp_par, mlp_feat, mlp_X, mlp_T, mlp_idx,
+      rent, sides, rlist, ops, shell, rshell, staging, partial, probe_in, probe_out, mlp_par, mlp_feat, mlp_X, mlp_T, mlp_idx,
       mlp_act, mlp_xin;
   size_t staging_doubles = 0, table_doubles = 0;
   int max_blocks = 0, nshell = 0;   // nshell: ghost cells of a padded block
@@ -77,6 +77,15 @@ size_t table_count(const icarus_grid_desc *d) {
     if (L < d->max_level) n += 2 * (N0 + N1 + N2);     // offsets
   }
   return n;
+}
+
+// ghost-fill work items a leaf can need at most: 32-task chunks of the ghost
+// cells of its 26 regions (all of them held by finer leaves)
+int items_per_block(const icarus_grid_desc *d) {
+  const int n0 = d->block[0], n1 = d->block[1], n2 = d->block[2];
+  auto chunks = [](int cells) { return (cells + 31) / 32; };
+  return 2 * (chunks(NGH * n1 * n2) + chunks(NGH * n0 * n2) + chunks(NGH * n0 * n1)) +
+         4 * (chunks(NGH * NGH * n0) + chunks(NGH * NGH * n1) + chunks(NGH * NGH * n2)) + 8 * chunks(NGH * NGH * NGH);
 }
 
 int shell_count(const icarus_grid_desc *d) {
@@ -142,12 +151,14 @@ Layout make_layout(const icarus_grid_desc *d) {
   L.vbg = L.add((size_t)nm * d->n_cells[0] * d->n_cells[1] * d->n_cells[2] * sizeof(double));
   L.scal = L.add((size_t)nm * 7 * sizeof(double) + 64);
   L.flags = L.add(mb);
-  L.lists = L.add(3 * mb * sizeof(int));        // all-leaf list + per-level lists + per-level coarse-fine lists
+  L.lists = L.add(2 * mb * sizeof(int));        // all-leaf list + per-level lists
+  L.rent = L.add((size_t)items_per_block(d) * mb * sizeof(int2));   // per level: ghost-fill work items
   L.sides = L.add(6 * mb * sizeof(int2));       // (slot, side) per level, per direction
   L.rlist = L.add(mb * sizeof(int));
   L.ops = L.add(amr ? mb * sizeof(MoveOp) : 0);
   L.nshell = shell_count(d);
   L.shell = L.add((size_t)L.nshell * sizeof(int));
+  L.rshell = L.add((size_t)(81 + L.nshell) * sizeof(int));   // region table, then the shell cells by region
   const size_t per_block = NVAR * ic;
   size_t chunk = std::max<size_t>(1, (size_t)(64u << 20) / (per_block * 8));
   chunk = std::min(chunk, mb);
@@ -201,6 +212,7 @@ void gauss_legendre(double *x, double *w) {
 
 struct icarus_ctx {
   icarus_grid_desc d{};
+  int nbd[MAXLEV + 2][3] = {};   // blocks per direction at each level (tree logic looks these up)
   Layout lay;
   int prec = 0;
   size_t rsize = 8;
@@ -225,7 +237,8 @@ struct icarus_ctx {
   unsigned int *status = nullptr;
   signed char *flags = nullptr;
   int *all_list = nullptr, *lvl_list = nullptr, *rlist = nullptr, *shell = nullptr;
-  int *cf_list = nullptr;   // per level: leaves with a coarser or finer leaf among their 26 neighbours
+  int2 *rent = nullptr;     // per level: (slot, region | finer << 8 | chunk << 9), up to 32 ghost tasks of a region held by coarser / finer leaves
+  int *rshell = nullptr;    // per region (start, group-first cells, cells), then the shell cells ordered by region
   int2 *sides = nullptr;
   MoveOp *ops = nullptr;
   // host mirrors
@@ -234,7 +247,8 @@ struct icarus_ctx {
   std::vector<int> mem_off;                 // first slot of each member
   std::vector<DevBlock> hblk;
   int lvl_count[MAXLEV + 1] = {0}, lvl_start[MAXLEV + 1] = {0};
-  int cf_count[MAXLEV + 1] = {0}, cf_start[MAXLEV + 1] = {0};
+  int rent_start[MAXLEV + 1] = {0}, rent_face[MAXLEV + 1] = {0}, rent_count[MAXLEV + 1] = {0};
+  int reg_tab[27][3] = {};  // per region: start in the region-ordered shell, group-first cells, cells
   int side_count[MAXLEV + 1][3] = {{0}}, side_start[MAXLEV + 1][3] = {{0}};
   int nrlist = 0, max_level_present = 1;
   std::vector<signed char> hflags;
@@ -299,7 +313,7 @@ uint64_t morton_key(const Leaf &l, int shift_to) {
   return key;
 }
 
-int nblk_dim(const icarus_ctx *c, int L, int d) { return (c->d.n_cells[d] / c->d.block[d]) << (L - 1); }
+int nblk_dim(const icarus_ctx *c, int L, int d) { return c->nbd[L][d]; }
 
 long long map_index(const icarus_ctx *c, int L, const int *b) {
   return ((long long)b[0] * nblk_dim(c, L, 1) + b[1]) * nblk_dim(c, L, 2) + b[2];
@@ -310,7 +324,9 @@ bool wrap_block(const icarus_ctx *c, int L, int *b) {
   for (int d = 0; d < 3; d++) {
     const int n = nblk_dim(c, L, d);
     if (c->d.bc_lo[d] == ICARUS_BC_PERIODIC) {
-      b[d] = ((b[d] % n) + n) % n;
+      if (b[d] < 0) b[d] += n;
+      else if (b[d] >= n) b[d] -= n;
+      if (b[d] < 0 || b[d] >= n) b[d] = ((b[d] % n) + n) % n;
     } else if (b[d] < 0 || b[d] >= n) {
       return false;
     }
@@ -393,8 +409,12 @@ void neighbours(const icarus_ctx *c, const Member &m, int n, std::vector<int> &o
 // most one level apart.
 bool tree_is_valid(icarus_ctx *c, Member &m) {
   const int top = c->d.max_level;
-  for (size_t n = 1; n < m.leaves.size(); n++)
-    if (!(morton_key(m.leaves[n - 1], top) < morton_key(m.leaves[n], top))) return false;
+  uint64_t prev = 0;
+  for (size_t n = 0; n < m.leaves.size(); n++) {
+    const uint64_t key = morton_key(m.leaves[n], top);
+    if (n > 0 && !(prev < key)) return false;
+    prev = key;
+  }
   if (!build_member_map(c, m)) return false;
   // coverage, counted in blocks of the finest level
   unsigned long long vol = 0;
@@ -447,7 +467,8 @@ icarus_status upload_tree(icarus_ctx *c, DevBlock *blk_dst) {
   c->hblk.assign(c->nleaves, DevBlock{});
   std::vector<int> nb27((size_t)c->nleaves * 27, -1);
   std::vector<int> all(c->nleaves);
-  std::vector<std::vector<int>> per_level(MAXLEV + 1), cf_level(MAXLEV + 1);
+  std::vector<std::vector<int>> per_level(MAXLEV + 1);
+  std::vector<std::vector<int2>> ent_face(MAXLEV + 1), ent_rest(MAXLEV + 1);
   std::vector<std::vector<int2>> sd[3];
   for (int k = 0; k < 3; k++) sd[k].assign(MAXLEV + 1, std::vector<int2>());
   std::vector<int> rl;
@@ -479,18 +500,27 @@ icarus_status upload_tree(icarus_ctx *c, DevBlock *blk_dst) {
         if (s == -2) finer = true;
       }
       if (finer) rl.push_back(slot);
-      // same-level leaves around the block (faces, edges, corners)
-      bool cf = false;
+      // same-level leaves around the block (faces, edges, corners); the
+      // regions held by coarser or finer leaves go to the ghost fill's
+      // entries (faces first)
       for (int dx = -1; dx <= 1; dx++)
         for (int dy = -1; dy <= 1; dy++)
           for (int dz = -1; dz <= 1; dz++) {
             int b[3] = {l.ix[0] + dx, l.ix[1] + dy, l.ix[2] + dz};
             if (!wrap_block(c, l.level, b)) continue;
             const int s = region_state(c, M, l.level, b);
-            if (s >= 0) nb27[(size_t)slot * 27 + (dx + 1) * 9 + (dy + 1) * 3 + (dz + 1)] = c->mem_off[m] + s;
-            else cf = true;
+            const int r = (dx + 1) * 9 + (dy + 1) * 3 + (dz + 1);
+            if (s >= 0) {
+              nb27[(size_t)slot * 27 + r] = c->mem_off[m] + s;
+            } else {
+              // work items of up to 32 tasks: 2x2x2 groups under a coarser
+              // leaf, cells next to finer ones
+              const bool face = (dx != 0) + (dy != 0) + (dz != 0) == 1, finer = s == -2;
+              const int tasks = finer ? c->reg_tab[r][2] : c->reg_tab[r][1];
+              for (int ch = 0; 32 * ch < tasks; ch++)
+                (face ? ent_face : ent_rest)[l.level].push_back(make_int2(slot, r | (finer ? 256 : 0) | ch << 9));
+            }
           }
-      if (cf) cf_level[l.level].push_back(slot);
       all[slot] = slot;
       per_level[l.level].push_back(slot);
       c->max_level_present = std::max(c->max_level_present, l.level);
@@ -507,15 +537,19 @@ icarus_status upload_tree(icarus_ctx *c, DevBlock *blk_dst) {
       for (size_t q = 0; q < mp.size(); q++) lm[o + q] = mp[q] >= 0 ? mp[q] + c->mem_off[m] : mp[q];
       o += (long long)mp.size();
     }
-  std::vector<int> lv, cfl;
+  std::vector<int> lv;
+  std::vector<int2> ent;
   for (int L = 1; L <= MAXLEV; L++) {
     c->lvl_start[L] = (int)lv.size();
     c->lvl_count[L] = (int)per_level[L].size();
     lv.insert(lv.end(), per_level[L].begin(), per_level[L].end());
-    c->cf_start[L] = (int)cfl.size();
-    c->cf_count[L] = (int)cf_level[L].size();
-    cfl.insert(cfl.end(), cf_level[L].begin(), cf_level[L].end());
+    c->rent_start[L] = (int)ent.size();
+    c->rent_face[L] = (int)ent_face[L].size();
+    c->rent_count[L] = (int)(ent_face[L].size() + ent_rest[L].size());
+    ent.insert(ent.end(), ent_face[L].begin(), ent_face[L].end());
+    ent.insert(ent.end(), ent_rest[L].begin(), ent_rest[L].end());
   }
+  if (ent.size() > (size_t)items_per_block(&c->d) * c->lay.max_blocks) return ICARUS_ERR_CAPACITY;
   std::vector<int2> sv;
   for (int L = 1; L <= MAXLEV; L++)
     for (int k = 0; k < 3; k++) {
@@ -538,7 +572,7 @@ icarus_status upload_tree(icarus_ctx *c, DevBlock *blk_dst) {
   CK(cudaMemcpyAsync(c->lmap_off, off.data(), sizeof(long long) * off.size(), cudaMemcpyHostToDevice, s));
   CK(cudaMemcpyAsync(c->all_list, all.data(), sizeof(int) * all.size(), cudaMemcpyHostToDevice, s));
   CK(cudaMemcpyAsync(c->lvl_list, lv.data(), sizeof(int) * lv.size(), cudaMemcpyHostToDevice, s));
-  if (!cfl.empty()) CK(cudaMemcpyAsync(c->cf_list, cfl.data(), sizeof(int) * cfl.size(), cudaMemcpyHostToDevice, s));
+  if (!ent.empty()) CK(cudaMemcpyAsync(c->rent, ent.data(), sizeof(int2) * ent.size(), cudaMemcpyHostToDevice, s));
   if (!sv.empty()) CK(cudaMemcpyAsync(c->sides, sv.data(), sizeof(int2) * sv.size(), cudaMemcpyHostToDevice, s));
   if (!rl.empty()) CK(cudaMemcpyAsync(c->rlist, rl.data(), sizeof(int) * rl.size(), cudaMemcpyHostToDevice, s));
   // host buffers above are freed on return: wait for the copies
@@ -837,16 +871,21 @@ struct ProfScope {
 // regrid get every ghost cell too.
 int enqueue_ghost(icarus_ctx *c, void *buf, double tfac, bool faces_only = false, bool skip_same = false) {
   int n = 0;
-  const int nshell = faces_only ? c->nshell_face : c->lay.nshell;
   for (int L = 1; L <= c->max_level_present; L++) {
     if (c->lvl_count[L] == 0) continue;
-    // skipping same-level ghosts leaves work only in leaves with a coarser or
-    // finer neighbour
-    const int *list = skip_same ? c->cf_list + c->cf_start[L] : c->lvl_list + c->lvl_start[L];
-    const int nlist = skip_same ? c->cf_count[L] : c->lvl_count[L];
-    if (nlist > 0) {
+    if (skip_same) {
+      // the ghost cells same-level leaves hold are read by the stage kernels
+      // from those leaves: only the regions held by coarser or finer leaves
+      const int ne = faces_only ? c->rent_face[L] : c->rent_count[L];
+      if (ne > 0) {
+        ProfScope p(c, 1);
+        ghost_regions_launch(c->kp, buf, c->prec, c->rent + c->rent_start[L], ne, c->rshell, L, c->stream);
+        n++;
+      }
+    } else {
       ProfScope p(c, 1);
-      ghost_neighbour_launch(c->kp, buf, c->prec, list, nlist, c->shell, nshell, L, skip_same, c->stream);
+      ghost_neighbour_launch(c->kp, buf, c->prec, c->lvl_list + c->lvl_start[L], c->lvl_count[L], c->shell,
+                             faces_only ? c->nshell_face : c->lay.nshell, L, c->stream);
       n++;
     }
     for (int dd = 0; dd < 3; dd++) {
@@ -1010,6 +1049,8 @@ icarus_status icarus_init_grid(const icarus_grid_desc *desc, icarus_ctx **out) {
   icarus_ctx *c = new (std::nothrow) icarus_ctx();
   if (!c) return ICARUS_ERR_ARG;
   c->d = *desc;
+  for (int L = 1; L <= MAXLEV + 1; L++)
+    for (int d = 0; d < 3; d++) c->nbd[L][d] = (desc->n_cells[d] / desc->block[d]) << (L - 1);
   c->lay = lay;
   c->prec = desc->precision == ICARUS_FP32_MIXED ? 1 : 0;
   c->rsize = c->prec ? 4 : 8;
@@ -1065,11 +1106,12 @@ icarus_status icarus_init_grid(const icarus_grid_desc *desc, icarus_ctx **out) {
   c->flags = at<signed char>(c, lay.flags);
   c->all_list = at<int>(c, lay.lists);
   c->lvl_list = c->all_list + lay.max_blocks;
-  c->cf_list = c->lvl_list + lay.max_blocks;
+  c->rent = at<int2>(c, lay.rent);
   c->sides = at<int2>(c, lay.sides);
   c->rlist = at<int>(c, lay.rlist);
   c->ops = lay.ops.bytes ? at<MoveOp>(c, lay.ops) : nullptr;
   c->shell = at<int>(c, lay.shell);
+  c->rshell = at<int>(c, lay.rshell);
   c->staging = at<double>(c, lay.staging);
   c->partial = at<double>(c, lay.partial);
   c->probe_in = at<double>(c, lay.probe_in);
@@ -1134,7 +1176,34 @@ icarus_status icarus_init_grid(const icarus_grid_desc *desc, icarus_ctx **out) {
     c->nshell_face = (int)sh.size();
     add(false, true);
     add(false, false);
+    // the same cells ordered by region (r = 9 (sx + 1) + 3 (sy + 1) + sz + 1
+    // with s the side of each coordinate: -1 low ghost, 0 interior, +1 high
+    // ghost), group-first cells first within a region; a table of (start,
+    // group-first cells, cells) per region ahead of them
+    std::vector<int> rs(81, 0);
+    auto side = [&](int p, int d) { return p < NGH ? -1 : (p >= NGH + desc->block[d] ? 1 : 0); };
+    for (int r = 0; r < 27; r++) {
+      const int want[3] = {r / 9 - 1, (r / 3) % 3 - 1, r % 3 - 1};
+      const int start = (int)rs.size() - 81;
+      int lead_n = 0;
+      for (int pass = 0; pass < 2 && r != 13; pass++)
+        for (int i = 0; i < P0; i++)
+          for (int j = 0; j < P1; j++)
+            for (int k = 0; k < P2; k++) {
+              if (side(i, 0) != want[0] || side(j, 1) != want[1] || side(k, 2) != want[2]) continue;
+              const bool lead = ((i | j | k) & 1) == 0;
+              if (lead != (pass == 0)) continue;
+              rs.push_back((i << 20) | (j << 10) | k);
+              if (lead) lead_n++;
+            }
+      rs[3 * r] = start;
+      rs[3 * r + 1] = lead_n;
+      rs[3 * r + 2] = (int)rs.size() - 81 - start;
+      for (int q = 0; q < 3; q++) c->reg_tab[r][q] = rs[3 * r + q];
+    }
     if (cudaMemcpyAsync(c->shell, sh.data(), sizeof(int) * sh.size(), cudaMemcpyHostToDevice, c->stream) !=
+            cudaSuccess ||
+        cudaMemcpyAsync(c->rshell, rs.data(), sizeof(int) * rs.size(), cudaMemcpyHostToDevice, c->stream) !=
             cudaSuccess ||
         cudaStreamSynchronize(c->stream) != cudaSuccess)
       return fail(ICARUS_ERR_CUDA);
@@ -1282,8 +1351,9 @@ icarus_status icarus_kernels_per_step(icarus_ctx *c, int *n) {
   for (int L = 1; L <= c->max_level_present; L++) {
     if (!c->lvl_count[L]) continue;
     // neighbour ghost pass of both fills (with direct halo reads only over
-    // the leaves that have a coarser or finer neighbour)
-    if (c->direct_halo ? c->cf_count[L] : c->lvl_count[L]) k += 2;
+    // the regions held by coarser or finer leaves: faces in the first fill)
+    if (c->direct_halo) k += (c->rent_face[L] > 0) + (c->rent_count[L] > 0);
+    else k += 2;
     for (int d = 0; d < 3; d++)
       if (c->side_count[L][d]) k += 2;   // physical ghost pass, both fills
   }
@@ -1743,11 +1813,7 @@ icarus_status icarus_regrid(icarus_ctx *c) {
   KParams kp_old = c->kp;
   std::vector<Member> old = std::move(c->mem);
   c->mem = std::move(next);
-  for (Member &M : c->mem) build_member_map(c, M);
-  // the level maps are only read through the new tables after the move
-  std::vector<DevBlock> old_hblk = c->hblk;
-  const int old_nleaves = c->nleaves;
-  (void)old_nleaves;
+  // the new level maps are built by the tree check after the move
   // upload the new block table into blk_alt first (the move kernel needs the
   // new block coordinates and the old table at the same time)
   icarus_status st;

@@ -141,11 +141,16 @@ int stage_tile_supported(int precision, int tj, int tk, int tracer);
 int stage_max_ctas_per_sm(int precision, int tj, int tk, int tracer);
 
 // ghost fill
-// skip_same: ghost cells held by a same-level leaf are left unfilled (the
-// stage kernels read them from that leaf directly), and physical-boundary
-// copies and prolongation read such cells from the neighbour as well
+// ghost_neighbour: every ghost cell of the listed leaves (copy, prolongation
+// or restriction); ghost_regions: work items of up to 32 cells (or 2x2x2
+// groups) of the regions around a leaf held by a coarser or finer leaf, while the ghost cells same-level leaves
+// hold are left unfilled (the stage kernels read them from those leaves, and
+// prolongation and the physical-boundary copies with skip_same read such
+// cells from the neighbour as well)
 void ghost_neighbour_launch(const KParams &kp, void *U, int precision, const int *list, int nlist,
-                            const int *shell, int nshell, int level, bool skip_same, cudaStream_t s);
+                            const int *shell, int nshell, int level, cudaStream_t s);
+void ghost_regions_launch(const KParams &kp, void *U, int precision, const int2 *items, int nitems,
+                          const int *rshell, int level, cudaStream_t s);
 void ghost_physical_launch(const KParams &kp, void *U, int precision, const int2 *sides, int nsides,
                            int dir, int level, double tshift_fac, bool faces_only, bool skip_same, cudaStream_t s);
 void reflux_launch(const KParams &kp, void *U, const void *flux, int precision, const int *list, int nlist,

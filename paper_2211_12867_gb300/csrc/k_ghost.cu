@@ -181,7 +181,7 @@ __device__ __forceinline__ bool restrict_in_block(const KParams &kp, const real 
 // ghost lies on (no divisions).
 template <typename real>
 __global__ void __launch_bounds__(256, sizeof(real) == 4 ? 4 : 2) k_ghost_neighbour(const KParams kp, real *U, const int *list, const int *shell, int nshell,
-                                  int L, int skip_same) {
+                                  int L) {
   const int s = blockIdx.y * blockDim.x + threadIdx.x;
   if (s >= nshell) return;
   const int slot = list[blockIdx.x];
@@ -205,15 +205,7 @@ __global__ void __launch_bounds__(256, sizeof(real) == 4 ? 4 : 2) k_ghost_neighb
   }
   real val[NVAR + 1];
   const int nv = kp.nvs;
-  if (skip_same) {
-    // a cell a same-level leaf holds: the stage kernels read it from there
-    int sd[3];
-#pragma unroll
-    for (int d = 0; d < 3; d++) sd[d] = p[d] < NGH ? -1 : (p[d] >= NGH + kp.nb[d] ? 1 : 0);
-    if (kp.nb27[(size_t)slot * 27 + (sd[0] + 1) * 9 + (sd[1] + 1) * 3 + (sd[2] + 1)] >= 0) return;
-  }
   const int o = lookup_block(kp, member, L, b);
-  if (o >= 0 && skip_same) return;
   if (o >= 0) {
 #pragma unroll
     for (int v = 0; v < NVAR + 1; v++)
@@ -234,7 +226,7 @@ __global__ void __launch_bounds__(256, sizeof(real) == 4 ? 4 : 2) k_ghost_neighb
       atomicOr(kp.status, ST_TREE);
       return;
     }
-    prolong_into<real>(kp, U, cs, L - 1, Ic, slot, p, skip_same != 0);
+    prolong_into<real>(kp, U, cs, L - 1, Ic, slot, p, false);
     return;
   } else {
     if (!restrict_in_block<real>(kp, U, member, L, b, q, G, val)) {
@@ -245,6 +237,67 @@ __global__ void __launch_bounds__(256, sizeof(real) == 4 ? 4 : 2) k_ghost_neighb
 #pragma unroll
   for (int v = 0; v < NVAR + 1; v++)
     if (v < nv) U[cell_index(kp, slot, v, p[0], p[1], p[2])] = val[v];
+}
+
+// Ghost cells of one region of a level-L leaf (one of the 26 around it, r =
+// 9 (sx + 1) + 3 (sy + 1) + sz + 1) that a coarser leaf holds (one lane per
+// 2 x 2 x 2 group, prolongation) or finer leaves hold (one lane per cell,
+// restriction).  A work item is up to 32 such tasks of one region, taken
+// by one warp: item = (slot, r | finer << 8 | chunk << 9), tasks 32 chunk
+// .. 32 chunk + 31 of the region-ordered shell list (group-first cells
+// first) behind its table of (start, group-first cells, cells) per region.
+// Same-level halo cells the prolongation's stencil reaches are read from
+// the neighbouring leaf (the step's fills leave those ghost copies unfilled).
+template <typename real>
+__global__ void __launch_bounds__(256, sizeof(real) == 4 ? 3 : 2) k_ghost_regions(const KParams kp, real *U, const int2 *items, int nitems, const int *rshell, int L) {
+  const int w = blockIdx.x * 8 + (threadIdx.x >> 5);
+  if (w >= nitems) return;
+  const int2 e = items[w];
+  const int slot = e.x, r = e.y & 255;
+  const bool finer = ((e.y >> 8) & 1) != 0;
+  const int t = ((e.y >> 9) << 5) + (threadIdx.x & 31);
+  if (t >= (finer ? rshell[3 * r + 2] : rshell[3 * r + 1])) return;
+  const int code = rshell[81 + rshell[3 * r] + t];
+  const int p[3] = {code >> 20, (code >> 10) & 1023, code & 1023};
+  const DevBlock B = kp.blk[slot];
+  const int side[3] = {r / 9 - 1, (r / 3) % 3 - 1, r % 3 - 1};
+  int b[3], q[3], G[3];
+#pragma unroll
+  for (int d = 0; d < 3; d++) {
+    // items exist only for neighbours inside the domain or across a
+    // periodic direction
+    const int nbl = kp.nbase[d] << (L - 1);
+    int bd = B.ix[d] + side[d];
+    if (bd < 0) bd += nbl;
+    else if (bd >= nbl) bd -= nbl;
+    b[d] = bd;
+    q[d] = p[d] - side[d] * kp.nb[d];   // padded index inside block b
+    G[d] = bd * kp.nb[d] + q[d] - NGH;
+  }
+  if (!finer) {
+    int cb[3], Ic[3];
+#pragma unroll
+    for (int d = 0; d < 3; d++) {
+      cb[d] = b[d] >> 1;
+      Ic[d] = G[d] >> 1;
+    }
+    const int cs = lookup_block(kp, B.member, L - 1, cb);
+    if (cs < 0) {
+      atomicOr(kp.status, ST_TREE);
+      return;
+    }
+    prolong_into<real>(kp, U, cs, L - 1, Ic, slot, p, true);
+  } else {
+    real val[NVAR + 1];
+    if (!restrict_in_block<real>(kp, U, B.member, L, b, q, G, val)) {
+      atomicOr(kp.status, ST_TREE);
+      return;
+    }
+    const int nv = kp.nvs;
+#pragma unroll
+    for (int v = 0; v < NVAR + 1; v++)
+      if (v < nv) U[cell_index(kp, slot, v, p[0], p[1], p[2])] = val[v];
+  }
 }
 
 // inner boundary state (FP64): map of the containing base cell, cone CME
@@ -520,13 +573,23 @@ __global__ void k_dt_from_max(const KParams kp, double cfl) {
 }  // namespace
 
 void ghost_neighbour_launch(const KParams &kp, void *U, int precision, const int *list, int nlist, const int *shell,
-                            int nshell, int level, bool skip_same, cudaStream_t s) {
+                            int nshell, int level, cudaStream_t s) {
   if (nlist <= 0) return;
   dim3 grid(nlist, (nshell + 255) / 256);
   if (precision)
-    k_ghost_neighbour<float><<<grid, 256, 0, s>>>(kp, (float *)U, list, shell, nshell, level, skip_same);
+    k_ghost_neighbour<float><<<grid, 256, 0, s>>>(kp, (float *)U, list, shell, nshell, level);
   else
-    k_ghost_neighbour<double><<<grid, 256, 0, s>>>(kp, (double *)U, list, shell, nshell, level, skip_same);
+    k_ghost_neighbour<double><<<grid, 256, 0, s>>>(kp, (double *)U, list, shell, nshell, level);
+}
+
+void ghost_regions_launch(const KParams &kp, void *U, int precision, const int2 *items, int nitems,
+                          const int *rshell, int level, cudaStream_t s) {
+  if (nitems <= 0) return;
+  const int grid = (nitems + 7) / 8;   // one warp per item
+  if (precision)
+    k_ghost_regions<float><<<grid, 256, 0, s>>>(kp, (float *)U, items, nitems, rshell, level);
+  else
+    k_ghost_regions<double><<<grid, 256, 0, s>>>(kp, (double *)U, items, nitems, rshell, level);
 }
 
 void ghost_physical_launch(const KParams &kp, void *U, int precision, const int2 *sides, int nsides, int dir,
