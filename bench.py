@@ -705,11 +705,12 @@ def main():
     kms, kcnt = g.profile_read()
     prof_step_ms = p0.elapsed_time(p1) / args.steps
     g.profile(False)
-    from paper_2211_12867_gb300.icarus import PROFILE_KINDS
+    from paper_2211_12867_gb300.icarus import PROFILE_KINDS, STEP_KINDS
+    kinds = PROFILE_KINDS[:STEP_KINDS]
     per_kernel = {k: {"launches": int(c), "avg_ms": (float(m) / c if c else None), "share": None}
-                  for k, m, c in zip(PROFILE_KINDS, kms, kcnt)}
-    tot = float(kms.sum())
-    for k, m in zip(PROFILE_KINDS, kms):
+                  for k, m, c in zip(kinds, kms, kcnt)}
+    tot = float(kms[:STEP_KINDS].sum())
+    for k, m in zip(kinds, kms):
         per_kernel[k]["share"] = float(m) / tot if tot > 0 else None
     hbm, peak_kind = peaks()
     corr_ms = per_kernel["stage_corrector"]["avg_ms"]

@@ -420,8 +420,11 @@ icarus_status icarus_profile(icarus_ctx *ctx, int enable);
 /* Device time (ms) and number of launches per kernel kind accumulated since
  * the previous read, then reset.  Kinds: 0 dt begin, 1 ghost fill from
  * neighbours, 2 physical-boundary ghosts, 3 predictor stage, 4 corrector
- * stage, 5 reflux, 6 dt finalize.  ms and count hold nkinds entries (<= 7).
- * Synchronises the stream. */
+ * stage, 5 reflux, 6 dt finalize, 7 refinement estimator (flagging), 8 regrid
+ * data movement, 9 CFL time step of the whole state (after a regrid or a
+ * state upload).  Kinds 7-9 are recorded by icarus_flag_refine and
+ * icarus_regrid while profiling is enabled.  ms and count hold nkinds
+ * entries (<= 10).  Synchronises the stream. */
 icarus_status icarus_profile_read(icarus_ctx *ctx, double *ms, int *count, int nkinds);
 
 /* Checkpoint and resume (the paper runs for days of simulated time; it has no

@@ -21,9 +21,9 @@ INCLUDE = os.path.join(os.path.dirname(HERE), "include")
 SOURCES = ["api.cu", "k_stage.cu", "k_ghost.cu", "k_amr.cu", "k_mlp.cu", "k_sums_static.cu", "k_peak.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 # host code without floating-point contraction: the geometry tables come out
-# bit for bit the same on every host architecture
+# bit for bit the same on every host architecture; OpenMP for the tree logic
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2",
-         "-Xcompiler", "-ffp-contract=off", "--expt-relaxed-constexpr"]
+         "-Xcompiler", "-ffp-contract=off", "-Xcompiler", "-fopenmp", "--expt-relaxed-constexpr"]
 
 
 def nvcc() -> str:
@@ -77,7 +77,7 @@ def build(force: bool = False, verbose_ptxas: bool = False) -> str:
             and all(os.path.getmtime(o) <= os.path.getmtime(LIB) for o in objs)):
         return LIB
     tmp = LIB + f".tmp{os.getpid()}"
-    cmd = [nvcc(), *ARCH, "-shared", "-o", tmp, *objs, "-lcudart"]
+    cmd = [nvcc(), *ARCH, "-shared", "-o", tmp, *objs, "-lcudart", "-lgomp"]
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:
         raise RuntimeError(f"link failed:\n{r.stdout}\n{r.stderr}")

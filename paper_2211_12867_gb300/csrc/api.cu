@@ -361,6 +361,10 @@ bool build_member_map(icarus_ctx *c, Member &m) {
 // index, -2 refined, -1 covered by a coarser leaf
 int region_state(const icarus_ctx *c, const Member &m, int L, const int *b) { return m.map[L][map_index(c, L, b)]; }
 
+// adjacent leaves of a leaf at most: 4 finer leaves per face, 2 per edge, 1
+// per corner
+constexpr int NB_MAX = 6 * 4 + 12 * 2 + 8;
+
 // adjacent leaves of leaf n (faces, edges, corners)
 void neighbours(const icarus_ctx *c, const Member &m, int n, std::vector<int> &out) {
   out.clear();
@@ -409,19 +413,20 @@ void neighbours(const icarus_ctx *c, const Member &m, int n, std::vector<int> &o
 // most one level apart.
 bool tree_is_valid(icarus_ctx *c, Member &m) {
   const int top = c->d.max_level;
-  uint64_t prev = 0;
-  for (size_t n = 0; n < m.leaves.size(); n++) {
-    const uint64_t key = morton_key(m.leaves[n], top);
-    if (n > 0 && !(prev < key)) return false;
-    prev = key;
-  }
+  const long long nl = (long long)m.leaves.size();
+  std::vector<uint64_t> key(nl);
+#pragma omp parallel for schedule(static)
+  for (long long n = 0; n < nl; n++) key[n] = morton_key(m.leaves[n], top);
+  for (long long n = 1; n < nl; n++)
+    if (!(key[n - 1] < key[n])) return false;
   if (!build_member_map(c, m)) return false;
   // coverage, counted in blocks of the finest level
   unsigned long long vol = 0;
   for (const Leaf &l : m.leaves) vol += 1ull << (3 * (top - l.level));
   if (vol != (unsigned long long)blocks_at_level(&c->d, top)) return false;
-  // 2:1 balance: no neighbour region two levels coarser or finer
-  for (const Leaf &l : m.leaves) {
+  // 2:1 balance: no neighbour region two levels coarser or finer (leaves
+  // checked in parallel; the maps are only read)
+  auto balanced = [&](const Leaf &l) {
     const int L = l.level;
     for (int dx = -1; dx <= 1; dx++)
       for (int dy = -1; dy <= 1; dy++)
@@ -450,8 +455,13 @@ bool tree_is_valid(icarus_ctx *c, Member &m) {
             }
           }
         }
-  }
-  return true;
+    return true;
+  };
+  int bad = 0;
+#pragma omp parallel for schedule(static) reduction(| : bad)
+  for (long long n = 0; n < nl; n++)
+    if (!balanced(m.leaves[n])) bad = 1;
+  return bad == 0;
 }
 
 // device tables that depend on the leaf lists
@@ -473,11 +483,32 @@ icarus_status upload_tree(icarus_ctx *c, DevBlock *blk_dst) {
   for (int k = 0; k < 3; k++) sd[k].assign(MAXLEV + 1, std::vector<int2>());
   std::vector<int> rl;
   c->max_level_present = 1;
+  // the relation of each leaf to the 27 regions around it (0 outside a
+  // non-periodic direction, 1 same-level leaf, 2 coarser, 3 finer) and the
+  // same-level neighbours, found in parallel (the maps are only read)
+  std::vector<unsigned char> rel((size_t)c->nleaves * 27, 0);
+  for (int m = 0; m < d.n_members; m++) {
+    const Member &M = c->mem[m];
+    const long long nl = (long long)M.leaves.size();
+#pragma omp parallel for schedule(static)
+    for (long long n = 0; n < nl; n++) {
+      const Leaf &l = M.leaves[n];
+      const size_t slot = (size_t)c->mem_off[m] + n;
+      for (int r = 0; r < 27; r++) {
+        int b[3] = {l.ix[0] + r / 9 - 1, l.ix[1] + (r / 3) % 3 - 1, l.ix[2] + r % 3 - 1};
+        if (!wrap_block(c, l.level, b)) continue;
+        const int s = region_state(c, M, l.level, b);
+        rel[slot * 27 + r] = s >= 0 ? 1 : (s == -2 ? 3 : 2);
+        if (s >= 0) nb27[slot * 27 + r] = c->mem_off[m] + s;
+      }
+    }
+  }
   for (int m = 0; m < d.n_members; m++) {
     const Member &M = c->mem[m];
     for (size_t n = 0; n < M.leaves.size(); n++) {
       const Leaf &l = M.leaves[n];
       const int slot = c->mem_off[m] + (int)n;
+      const unsigned char *rs = rel.data() + (size_t)slot * 27;
       DevBlock &B = c->hblk[slot];
       B.member = m;
       B.level = l.level;
@@ -487,40 +518,28 @@ icarus_status upload_tree(icarus_ctx *c, DevBlock *blk_dst) {
       bool finer = false;
       for (int f = 0; f < 6; f++) {
         const int dd = f / 2, hi = f % 2;
-        int b[3] = {l.ix[0], l.ix[1], l.ix[2]};
-        b[dd] += hi ? 1 : -1;
-        if (!wrap_block(c, l.level, b)) {
+        const int r = 13 + (hi ? 1 : -1) * (dd == 0 ? 9 : (dd == 1 ? 3 : 1));
+        if (rs[r] == 0) {
           B.nbr[f] = NB_PHYS;
           B.phys |= 1 << f;
           sd[dd][l.level].push_back(make_int2(slot, hi));
           continue;
         }
-        const int s = region_state(c, M, l.level, b);
-        B.nbr[f] = s >= 0 ? NB_SAME : (s == -2 ? NB_FINER : NB_COARSER);
-        if (s == -2) finer = true;
+        B.nbr[f] = rs[r] == 1 ? NB_SAME : (rs[r] == 3 ? NB_FINER : NB_COARSER);
+        if (rs[r] == 3) finer = true;
       }
       if (finer) rl.push_back(slot);
-      // same-level leaves around the block (faces, edges, corners); the
-      // regions held by coarser or finer leaves go to the ghost fill's
-      // entries (faces first)
-      for (int dx = -1; dx <= 1; dx++)
-        for (int dy = -1; dy <= 1; dy++)
-          for (int dz = -1; dz <= 1; dz++) {
-            int b[3] = {l.ix[0] + dx, l.ix[1] + dy, l.ix[2] + dz};
-            if (!wrap_block(c, l.level, b)) continue;
-            const int s = region_state(c, M, l.level, b);
-            const int r = (dx + 1) * 9 + (dy + 1) * 3 + (dz + 1);
-            if (s >= 0) {
-              nb27[(size_t)slot * 27 + r] = c->mem_off[m] + s;
-            } else {
-              // work items of up to 32 tasks: 2x2x2 groups under a coarser
-              // leaf, cells next to finer ones
-              const bool face = (dx != 0) + (dy != 0) + (dz != 0) == 1, finer = s == -2;
-              const int tasks = finer ? c->reg_tab[r][2] : c->reg_tab[r][1];
-              for (int ch = 0; 32 * ch < tasks; ch++)
-                (face ? ent_face : ent_rest)[l.level].push_back(make_int2(slot, r | (finer ? 256 : 0) | ch << 9));
-            }
-          }
+      // the regions held by coarser or finer leaves go to the ghost fill's
+      // work items of up to 32 tasks (2x2x2 groups under a coarser leaf,
+      // cells next to finer ones), face regions first
+      for (int r = 0; r < 27; r++) {
+        if (rs[r] < 2) continue;
+        const int dx = r / 9 - 1, dy = (r / 3) % 3 - 1, dz = r % 3 - 1;
+        const bool face = (dx != 0) + (dy != 0) + (dz != 0) == 1, fin = rs[r] == 3;
+        const int tasks = fin ? c->reg_tab[r][2] : c->reg_tab[r][1];
+        for (int ch = 0; 32 * ch < tasks; ch++)
+          (face ? ent_face : ent_rest)[l.level].push_back(make_int2(slot, r | (fin ? 256 : 0) | ch << 9));
+      }
       all[slot] = slot;
       per_level[l.level].push_back(slot);
       c->max_level_present = std::max(c->max_level_present, l.level);
@@ -1004,6 +1023,7 @@ icarus_status poll_status(icarus_ctx *c) {
 
 icarus_status recompute_dt(icarus_ctx *c) {
   CK(cudaMemsetAsync(c->inv_max, 0, sizeof(unsigned long long) * c->d.n_members, c->stream));
+  ProfScope p(c, 9);
   dt_full_launch(c->kp, c->U, c->prec, c->nleaves, c->d.cfl, c->stream);
   CK(cudaPeekAtLastError());
   return ICARUS_OK;
@@ -1672,8 +1692,10 @@ icarus_status icarus_flag_refine(icarus_ctx *c, const icarus_refine *crit, int8_
                          (double)which};
     if (!(w[0] >= 0.0) || !(w[1] < M_PI) || !(w[2] < M_PI) || !(w[3] < M_PI) || !(w[4] >= 0.0))
       return ICARUS_ERR_ARG;
+    ProfScope p(c, 7);
     shock_estimator_launch(c->kp, c->U, c->prec, 0, c->nleaves, w, c->flags, c->stream);
   } else {
+    ProfScope p(c, 7);
     estimator_launch(c->kp, c->U, c->prec, 0, c->nleaves, crit->e_refine, crit->e_coarsen, crit->eps, crit->dv,
                      c->flags, c->stream);
   }
@@ -1740,19 +1762,26 @@ icarus_status icarus_regrid(icarus_ctx *c) {
         for (int q = 0; q < 8; q++) T[i + q] = l.level - 1;
     }
     // 2:1 balance, least fixed point
-    // neighbour lists in one flat array (offsets per leaf)
-    std::vector<int> nb_off(n + 1, 0), nb_all, tmp;
-    nb_all.reserve((size_t)n * 26);
-    for (int i = 0; i < n; i++) {
-      neighbours(c, M, i, tmp);
-      nb_all.insert(nb_all.end(), tmp.begin(), tmp.end());
-      nb_off[i + 1] = (int)nb_all.size();
+    // neighbour lists in one flat array, NB_MAX per leaf (found in parallel:
+    // the lookups only read the member's maps)
+    std::vector<int> nb_cnt(n), nb_all((size_t)n * NB_MAX);
+#pragma omp parallel
+    {
+      std::vector<int> tmp;
+      tmp.reserve(NB_MAX);
+#pragma omp for schedule(static)
+      for (int i = 0; i < n; i++) {
+        neighbours(c, M, i, tmp);
+        const int k = std::min<int>((int)tmp.size(), NB_MAX);
+        std::copy(tmp.begin(), tmp.begin() + k, nb_all.begin() + (size_t)i * NB_MAX);
+        nb_cnt[i] = k;
+      }
     }
     bool changed = true;
     while (changed) {
       changed = false;
       for (int i = 0; i < n; i++) {
-        for (int e = nb_off[i]; e < nb_off[i + 1]; e++) {
+        for (int e = i * NB_MAX; e < i * NB_MAX + nb_cnt[i]; e++) {
           const int j = nb_all[e];
           if (T[j] > T[i] + 1) {
             if (T[i] < M.leaves[i].level) {
@@ -1832,7 +1861,10 @@ icarus_status icarus_regrid(icarus_ctx *c) {
       }
     CK(cudaMemcpyAsync(c->blk_alt, nb.data(), sizeof(DevBlock) * nb.size(), cudaMemcpyHostToDevice, c->stream));
     CK(cudaMemcpyAsync(c->ops, ops.data(), sizeof(MoveOp) * ops.size(), cudaMemcpyHostToDevice, c->stream));
-    regrid_move_launch2(kp_old, c->U, c->Ualt, c->blk_alt, c->prec, c->ops, (int)ops.size(), c->stream);
+    {
+      ProfScope p(c, 8);
+      regrid_move_launch2(kp_old, c->U, c->Ualt, c->blk_alt, c->prec, c->ops, (int)ops.size(), c->stream);
+    }
     CK(cudaPeekAtLastError());
     CK(cudaStreamSynchronize(c->stream));
   }
@@ -1880,7 +1912,7 @@ icarus_status icarus_profile(icarus_ctx *c, int enable) {
 }
 
 icarus_status icarus_profile_read(icarus_ctx *c, double *ms, int *count, int nkinds) {
-  if (!c || !ms || !count || nkinds < 1 || nkinds > 7) return ICARUS_ERR_ARG;
+  if (!c || !ms || !count || nkinds < 1 || nkinds > 10) return ICARUS_ERR_ARG;
   CK(cudaStreamSynchronize(c->stream));
   for (int k = 0; k < nkinds; k++) {
     ms[k] = 0.0;

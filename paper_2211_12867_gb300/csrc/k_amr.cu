@@ -84,9 +84,14 @@ __global__ void k_estimator(const KParams kp, const real *U, int slot0, double e
   const size_t nbc = (size_t)kp.n_base_cells[0] * kp.n_base_cells[1] * kp.n_base_cells[2];
   const double *vbg = kp.vbg + (size_t)B.member * nbc;
   int refine = 0, keep = 0;
+  // one refining cell settles the leaf's flag: the threads stop once any of
+  // them has found one (s_refine), which leaves the flag unchanged
+  __shared__ volatile int s_refine;
+  if (threadIdx.x == 0) s_refine = 0;
+  __syncthreads();
   // without a recorded background the gate is closed everywhere: no cell
   // counts and the block is flagged for coarsening
-  for (int c = has_bg ? threadIdx.x : kp.icells; c < kp.icells; c += blockDim.x) {
+  for (int c = has_bg ? threadIdx.x : kp.icells; c < kp.icells && !s_refine; c += blockDim.x) {
     const int k = c % kp.nb[2], j = (c / kp.nb[2]) % kp.nb[1], i = c / (kp.nb[2] * kp.nb[1]);
     const int p0 = i + NGH, p1 = j + NGH, p2 = k + NGH;
     // the speed gate first: E only matters where it is open, and not at all
@@ -121,7 +126,10 @@ __global__ void k_estimator(const KParams kp, const real *U, int slot0, double e
     const double er = loehner(rm, u0[0], rp, eps);
     const double ep = loehner(pm, est_pressure(u0, kp.gamma), pp, eps);
     const double E = er > ep ? er : ep;
-    if (E > e_ref) refine = 1;
+    if (E > e_ref) {
+      refine = 1;
+      s_refine = 1;
+    }
     if (E > e_crs) keep = 1;
   }
   refine = __syncthreads_or(refine);
@@ -162,7 +170,11 @@ __global__ void k_shock_estimator(const KParams kp, const real *U, int slot0, do
   const double lon_e = __dsub_rn(E.lon0, __dmul_rn(E.rate, __dsub_rn(t, E.t0)));
   const bool sph = kp.geometry == 0;
   int refine = 0;
-  for (int c = threadIdx.x; c < kp.icells && !refine; c += blockDim.x) {
+  // one refining cell settles the leaf's flag (see k_estimator)
+  __shared__ volatile int s_refine;
+  if (threadIdx.x == 0) s_refine = 0;
+  __syncthreads();
+  for (int c = threadIdx.x; c < kp.icells && !refine && !s_refine; c += blockDim.x) {
     const int k = c % kp.nb[2], j = (c / kp.nb[2]) % kp.nb[1], i = c / (kp.nb[2] * kp.nb[1]);
     const int I = B.ix[0] * kp.nb[0] + i + NGH, J = B.ix[1] * kp.nb[1] + j + NGH, K = B.ix[2] * kp.nb[2] + k + NGH;
     const double th = G.tc[J], ph = G.pc[K];
@@ -174,6 +186,7 @@ __global__ void k_shock_estimator(const KParams kp, const real *U, int slot0, do
     const int p0 = i + NGH, p1 = j + NGH, p2 = k + NGH;
     if (which >= 1 && vel(kp, U, slot, TRV, p0, p1, p2) > x_thr) {
       refine = 1;
+      s_refine = 1;
       continue;
     }
     if (which == 1) continue;
@@ -196,7 +209,10 @@ __global__ void k_shock_estimator(const KParams kp, const real *U, int slot0, do
       e = __ddiv_rn(__dsub_rn(vpp, vpm), __dsub_rn(qp, qm));
     }
     const double div = __dadd_rn(__dadd_rn(a, b), e);
-    if (div < -div_thr) refine = 1;
+    if (div < -div_thr) {
+      refine = 1;
+      s_refine = 1;
+    }
   }
   refine = __syncthreads_or(refine);
   if (threadIdx.x == 0) flags[blockIdx.x] = refine ? 1 : -1;

@@ -377,11 +377,12 @@ class Icarus:
         _chk("icarus_profile", self.lib.icarus_profile(self.ctx, int(bool(enable))))
 
     def profile_read(self):
-        """(ms[7], count[7]) per kernel kind since the last read (see PROFILE_KINDS)."""
-        ms = np.zeros(7)
-        cnt = np.zeros(7, dtype=np.int32)
+        """(ms, count) per kernel kind since the last read (see PROFILE_KINDS)."""
+        nk = len(PROFILE_KINDS)
+        ms = np.zeros(nk)
+        cnt = np.zeros(nk, dtype=np.int32)
         _chk("icarus_profile_read", self.lib.icarus_profile_read(self.ctx, _dp(ms),
-                                                                 cnt.ctypes.data_as(C.POINTER(C.c_int)), 7))
+                                                                 cnt.ctypes.data_as(C.POINTER(C.c_int)), nk))
         return ms, cnt
 
 
@@ -461,7 +462,8 @@ class Icarus:
 MLP_PARAMS = 128 * 64 + 128 + 128 * 128 + 128 + 128 + 1
 
 PROFILE_KINDS = ["dt_begin", "ghost_neighbour", "ghost_physical", "stage_predictor", "stage_corrector",
-                 "reflux", "dt_finalize"]
+                 "reflux", "dt_finalize", "estimator", "regrid_move", "dt_full"]
+STEP_KINDS = 7   # the first seven kinds are the step's launches
 
 
 def conservation_sums_static(g, member=0):

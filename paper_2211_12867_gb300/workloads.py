@@ -110,19 +110,21 @@ def run_cme(g, cmes, *, t_inj, hours_after=72.0, regrid_every=10, max_levels=Non
 
 def step_profile(g, n_steps=20, crit=None, repeats=3):
     """Where the time of an AMR step goes: per kernel kind of the step (CUDA
-    events, graph replay off while profiling) and the host-timed cost of one
-    flag + regrid; returns a JSON-ready dict (per step / per regrid)."""
-    from .icarus import PROFILE_KINDS
+    events, graph replay off while profiling), the host-timed cost of a flag
+    and a regrid, and the device time of the first flag + regrid per kernel
+    kind (the rest of its wall time is host work and synchronisation);
+    returns a JSON-ready dict (per step / per regrid)."""
+    from .icarus import PROFILE_KINDS, STEP_KINDS
     g.profile(True)
     g.profile_read()
     g.step(n_steps)
     ms, cnt = g.profile_read()
-    g.profile(False)
-    tot = float(ms.sum())
+    tot = float(ms[:STEP_KINDS].sum())
     kinds = {k: {"ms_per_step": float(ms[i]) / n_steps, "launches_per_step": int(cnt[i]) / n_steps,
-                 "share": float(ms[i]) / tot if tot > 0 else None} for i, k in enumerate(PROFILE_KINDS)}
+                 "share": float(ms[i]) / tot if tot > 0 else None} for i, k in enumerate(PROFILE_KINDS[:STEP_KINDS])}
     t_flag = t_regrid = 0.0
     done = 0
+    regrid_device = None
     for _ in range(repeats):
         w0 = time.perf_counter()
         g.flag_refine(**(crit or CRIT))
@@ -133,11 +135,17 @@ def step_profile(g, n_steps=20, crit=None, repeats=3):
             if e.code != H.CAPACITY:
                 raise
         w2 = time.perf_counter()
+        if regrid_device is None:
+            fms, fcnt = g.profile_read()
+            regrid_device = {k: float(fms[i]) for i, k in enumerate(PROFILE_KINDS) if fcnt[i] > 0}
+            g.profile(False)
         t_flag += w1 - w0
         t_regrid += w2 - w1
         done += 1
+    g.profile(False)
     return {"kernels_ms_per_step": tot / n_steps, "kernels": kinds, "leaves": g.n_leaves(-1),
-            "flag_ms": 1e3 * t_flag / done, "regrid_ms": 1e3 * t_regrid / done}
+            "flag_ms": 1e3 * t_flag / done, "regrid_ms": 1e3 * t_regrid / done,
+            "flag_regrid_device_ms": regrid_device}
 
 
 def run_learned_window(g, *, n_regrids, regrid_every, max_level, crit=None, t_stop=np.inf):
