@@ -381,7 +381,10 @@ icarus_status icarus_mlp_set_params(icarus_ctx *ctx, const float *host, size_t n
 icarus_status icarus_mlp_get_params(icarus_ctx *ctx, float *host, size_t n);
 
 /* Features of every leaf (global leaf order) after a ghost fill; host_out
- * (optional) receives n_leaves x 64 floats. */
+ * (optional) receives n_leaves x 64 floats.  The 4 x 4 x 4 sub-cubes need
+ * block sizes that are multiples of 4 (else ICARUS_ERR_ARG); each sub-cube
+ * mean is summed in a fixed order, so the features are the same bits on
+ * every call. */
 icarus_status icarus_mlp_features(icarus_ctx *ctx, float *host_out);
 
 /* Refinement probability of every leaf (features + forward), host n_leaves. */

@@ -1701,6 +1701,8 @@ icarus_status icarus_flag_refine(icarus_ctx *c, const icarus_refine *crit, int8_
   }
   if (crit->mode == ICARUS_FLAG_LEARNED) {
     if (!c->mlp_ready) return ICARUS_ERR_STATE;
+    for (int k = 0; k < 3; k++)
+      if (c->d.block[k] % 4) return ICARUS_ERR_ARG;   // the features' sub-cubes
     mlp_leaf_probabilities(c);
     mlp_combine_launch(c->mlp_prob, c->blk, c->flags, c->nleaves, c->stream);
   }

@@ -32,14 +32,16 @@ __host__ __device__ inline MlpView mlp_view(const float *th) {
   return m;
 }
 
+// One warp per sub-cube (4 x 4 x 4 sub-cubes of s0 x s1 x s2 cells with
+// s = n / 4; cells past 4 s in a direction belong to none): the lanes take
+// the sub-cube's cells in a fixed stride, add in FP64 and reduce in a fixed
+// shuffle tree, so the features are the same bits on every run and for
+// every member.
 template <typename real>
 __global__ void k_features(const KParams kp, const real *U, int slot0, float *out) {
-  __shared__ float sums[64];
   const int slot = slot0 + blockIdx.x;
-  if (threadIdx.x < 64) sums[threadIdx.x] = 0.f;
-  __syncthreads();
   const int n0 = kp.nb[0], n1 = kp.nb[1], n2 = kp.nb[2];
-  const int s0 = n0 / 4, s1 = n1 / 4, s2 = n2 / 4;
+  const int s0 = n0 / 4, s1 = n1 / 4, s2 = n2 / 4, per = s0 * s1 * s2;
   const double gm1 = kp.gamma - 1.0;
   auto cell = [&](int v, int i, int j, int k) -> double {
     return (double)U[((((size_t)slot * kp.nvs + v) * kp.P[0] + i) * kp.P[1] + j) * kp.P[2] + k];
@@ -51,32 +53,35 @@ __global__ void k_features(const KParams kp, const real *U, int slot0, float *ou
     w[1] = m1 / r;
     w[2] = gm1 * (cell(4, i, j, k) - 0.5 * (m1 * m1 + m2 * m2 + m3 * m3) / r - 0.5 * (b1 * b1 + b2 * b2 + b3 * b3));
   };
-  for (int c = threadIdx.x; c < kp.icells; c += blockDim.x) {
-    const int k = c % n2, j = (c / n2) % n1, i = c / (n2 * n1);
-    const int p0 = i + NGH, p1 = j + NGH, p2 = k + NGH;
-    double w0[3], wm[3][3], wp[3][3];
-    prims(p0, p1, p2, w0);
-    prims(p0 - 1, p1, p2, wm[0]);
-    prims(p0 + 1, p1, p2, wp[0]);
-    prims(p0, p1 - 1, p2, wm[1]);
-    prims(p0, p1 + 1, p2, wp[1]);
-    prims(p0, p1, p2 - 1, wm[2]);
-    prims(p0, p1, p2 + 1, wp[2]);
-    double g = 0.0;
-    for (int q = 0; q < 3; q++) {
-      double s = 0.0;
-      for (int d = 0; d < 3; d++) {
-        const double cd = 0.5 * (wp[d][q] - wm[d][q]);
-        s += cd * cd;
+  const int lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+  for (int sc = threadIdx.x >> 5; sc < 64; sc += nw) {
+    const int a = sc / 16, b = (sc / 4) % 4, cc = sc % 4;
+    double acc = 0.0;
+    for (int t = lane; t < per; t += 32) {
+      const int i = a * s0 + t / (s1 * s2), j = b * s1 + (t / s2) % s1, k = cc * s2 + t % s2;
+      const int p0 = i + NGH, p1 = j + NGH, p2 = k + NGH;
+      double w0[3], wm[3][3], wp[3][3];
+      prims(p0, p1, p2, w0);
+      prims(p0 - 1, p1, p2, wm[0]);
+      prims(p0 + 1, p1, p2, wp[0]);
+      prims(p0, p1 - 1, p2, wm[1]);
+      prims(p0, p1 + 1, p2, wp[1]);
+      prims(p0, p1, p2 - 1, wm[2]);
+      prims(p0, p1, p2 + 1, wp[2]);
+      double g = 0.0;
+      for (int q = 0; q < 3; q++) {
+        double s = 0.0;
+        for (int d = 0; d < 3; d++) {
+          const double cd = 0.5 * (wp[d][q] - wm[d][q]);
+          s += cd * cd;
+        }
+        g += sqrt(s) / (fabs(w0[q]) + 1e-30);
       }
-      g += sqrt(s) / (fabs(w0[q]) + 1e-30);
+      acc += g / 3.0;
     }
-    g /= 3.0;
-    const int sc = ((i / s0) * 4 + j / s1) * 4 + k / s2;
-    atomicAdd(&sums[sc], (float)g);
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+    if (lane == 0) out[(size_t)blockIdx.x * 64 + sc] = (float)(acc / per);
   }
-  __syncthreads();
-  if (threadIdx.x < 64) out[(size_t)blockIdx.x * 64 + threadIdx.x] = sums[threadIdx.x] / (float)(s0 * s1 * s2);
 }
 
 // forward over rows of X (row index list `idx` or identity), 4 samples per CTA

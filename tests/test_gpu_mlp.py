@@ -48,6 +48,25 @@ def test_features_match_oracle():
         assert np.allclose(F[n], ref, rtol=2e-5, atol=1e-7), n
 
 
+def test_features_are_deterministic():
+    """The features of a leaf are the same bits on every call and for every
+    ensemble member holding the same state (the sub-cube sums reduce in a
+    fixed order)."""
+    g, o = make_pair(n=(48, 24, 48), nb=(12, 12, 12), n_members=2, **STR)
+    wind_setup(g, o, member=0)
+    wind_setup(g, o, member=1)
+    g.step(10)
+    F1, F2 = g.mlp_features(), g.mlp_features()
+    assert np.array_equal(F1, F2)
+    n0 = g.n_leaves(0)
+    assert np.array_equal(F1[:n0], F1[n0:])
+    o.set_state(g.get_state(0))
+    o.ghost_fill()
+    for n in range(o.nleaves):
+        ref = M.features_from_padded(o.get_padded(n, 0), 1.5)
+        assert np.allclose(F1[n], ref, rtol=2e-5, atol=1e-7), n
+
+
 def test_forward_and_gradient_match_oracle():
     g, _ = make_pair(n=(24, 12, 12), nb=(12, 12, 12), **STR)
     rng = np.random.default_rng(0)
