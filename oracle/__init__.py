@@ -4,9 +4,9 @@ TEST INFRASTRUCTURE ONLY.  Only ``tests/``, ``__graft_entry__.smoke()`` and
 the CPU-baseline leg of ``bench.py`` may import this package.  It shares no
 code with the CUDA library in ``paper_2211_12867_gb300``: its C sources
 (``or_physics.c``, ``or_grid.c``) implement the method independently, in FP64,
-in natural loop order, from the paper (Sect. 2.1, 2.2, 3, Eqs. 1-5) and the
-readings recorded in the design notes.  ``mlp.py`` holds the NumPy oracle of
-the learned refinement predictor.
+in natural loop order, from the paper (Sect. 2.1, 2.2, 3, Eqs. 1-5); where
+the paper is silent the C sources state the reading they take at each use.
+``mlp.py`` holds the NumPy oracle of the learned refinement predictor.
 
 Every routine here is pinned by ``tests/test_oracle_*.py`` against closed
 forms, invariants, textbook solutions and the numbers the paper prints.

@@ -11,8 +11,8 @@
  *   Sect. 3    block AMR, factor 2 per level in every direction, neighbours
  *              differ by at most one level, blocks coarsen when the criterion
  *              no longer holds.
- * Where the paper is silent the readings R2-R16 of the design notes are
- * implemented (each is named at its use below).
+ * Where the paper is silent a reading is taken; each is stated at its use
+ * below (tagged R2 ... R19).
  *
  * Everything is FP64 in natural loop order; no blocking, no fusion.
  */

@@ -2,8 +2,8 @@
 
 * wedge   — 512 x 60 x 180 equidistant single-level wedge, 0.1-2 AU.
 * amr     — radially stretched 264 x 36 x 96 base grid (q = 20^(1/264),
-            12^3 blocks, 528 base blocks; the survey's reading of the
-            256 x 30 x 90 garble), solution AMR up to level 4 with the
+            12^3 blocks, 528 base blocks; 256 x 30 x 90 as printed does
+            not divide into 12^3 blocks), solution AMR up to level 4 with the
             Loehner + speed-gate criterion, regrid every 10 steps.
 * ensemble — 32 cone-CME draws on the amr grid, levels 3 or 4 per member.
 * learned — the amr grid at level 5 with the learned pre-flagger.
