@@ -276,12 +276,17 @@ __global__ void __launch_bounds__(stage_threads(TJ, TK), stage_min_ctas(sizeof(r
     };
     // radial face between planes p-1 and p from the slopes at both planes
     auto rflux = [&](int p, const real *sm, const real *sp, real *F) {
-      real b[NVAR], c[NVAR], WL[NVAR], WR[NVAR];
+      real b[NVAR], c[NVAR];
       gather(ringp(p - 1), jl + 2, kl + 2, b);
       gather(ringp(p), jl + 2, kl + 2, c);
-      axpy8<real>(b, real(1), sm, WL);
-      axpy8<real>(c, real(-1), sp, WR);
-      tvdlf_states<real, 0>(WL, WR, b, c, gamma, igm1, F);
+      if constexpr (sizeof(real) == 4) {
+        tvdlf_pair<0>(b, c, sm, sp, gamma, igm1, F);
+      } else {
+        real WL[NVAR], WR[NVAR];
+        axpy8<real>(b, real(1), sm, WL);
+        axpy8<real>(c, real(-1), sp, WR);
+        tvdlf_states<real, 0>(WL, WR, b, c, gamma, igm1, F);
+      }
     };
     // div B at plane p on the (TJ+2) x (TK+2) positions around the tile
     auto divb_plane = [&](int p) {
