@@ -352,9 +352,10 @@ icarus_status icarus_set_fp64_islands(icarus_ctx *ctx, double p_over_e, double b
 
 /* How the stage kernels get halo cells that a same-level leaf holds: 1 (the
  * default) reads them from that leaf's interior, and the step's ghost fills
- * skip them; 0 fills every ghost cell before each stage and reads the ghost
- * layer.  Both give the same bits; the switch exists for tests and
- * measurements. */
+ * cover only the regions around each leaf that coarser or finer leaves hold
+ * (plus the physical boundaries); 0 fills every ghost cell before each stage
+ * and reads the ghost layer.  Both give the same bits; the switch exists for
+ * tests and measurements. */
 icarus_status icarus_set_direct_halo(icarus_ctx *ctx, int enable);
 
 /* Capture one step of the launch sequence in a CUDA graph and replay it in
